@@ -1,0 +1,466 @@
+"""Plain FP64 CPU oracle of the FFT-Galerkin Newton-CG method.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU
+baseline leg of the benchmark may import this module; the product path never
+calls it and shares no code with it.
+
+Everything is written in full 3x3 tensor notation, in float64, vectorised
+over voxels but otherwise in the order the paper states it:
+
+* grid and frequencies ............ Section 2.3 (reduced index set, odd N)
+* DFT pair F, F^-1 ................ Eq. (DFT_forward_inverse); numpy's FFT is
+                                    the library primitive, scaled to the
+                                    paper's convention (1/|N| on the forward)
+* projection G = F^-1 Ghat F ...... Eq. (discrete_projection), Ghat from the
+                                    closed form of Appendix A, Eq. (FT_projection)
+* reference-medium Green operator . Appendix A, Eq. (Gamma_explicit), used only
+                                    to pin Ghat by an independent formula
+* J2 return mapping and tangent ... Section 4.2 (n = 1: linear hardening)
+* CG on G C de = -G sigma ......... Eq. (linear_system), Section 2.5
+* Newton increment loop ........... Algorithm 1
+* homogenised stress .............. Eq. (trapz): the mean of the nodal stress
+* macroscopic 6x6 tangent ......... not in the paper (FE^2 context of
+                                    Section 1); six linear solves with the
+                                    converged tangent
+
+Readings of the paper taken here (each also listed in the design notes):
+* plastic iff Phi_trial > 1e-12 * sigma_0 (tie-break at the yield surface);
+* Newton stops on ||de*|| / ||E||_field <= eta_NW with the field L2 norm and
+  ||E||_field = sqrt(V) ||E||_F, after at least one iteration;
+* CG stops on the recursive residual ||r_j|| / ||r_0|| <= eta_CG, x_0 = 0;
+  a right-hand side at roundoff level, ||G sigma|| <= 1e-13 ||sigma||, is
+  already in equilibrium and takes no CG iteration (de = 0), and CG also
+  stops once ||r_j|| <= 1e-13 ||tau||, tau the field whose projection is the
+  right-hand side (sigma, or C : E_j for the macroscopic tangent): below that
+  floor the residual is FFT roundoff, which has an incompatible part that CG
+  cannot remove, and iterating on it makes the iterate diverge;
+* the history is committed from one last constitutive call at the converged
+  strain, and the converged eps* is the initial guess of the next increment.
+
+Field layout: full tensors [3, 3, N, N, N] (x1 slowest). The 6-component
+order used at the library boundary is (11, 22, 33, 23, 13, 12).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PAIRS = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+
+# A residual below this fraction of the norm of the field it was projected
+# from is FFT roundoff (see the readings above).
+ROUNDOFF_RHS = 1e-13
+
+I2 = np.eye(3)
+II = np.einsum("ij,lm->ijlm", I2, I2)
+I4s = 0.5 * (np.einsum("il,jm->ijlm", I2, I2) + np.einsum("im,jl->ijlm", I2, I2))
+I4d = I4s - II / 3.0
+
+
+# --------------------------------------------------------------------------
+# 6-component <-> full tensor conversion (boundary convention only)
+# --------------------------------------------------------------------------
+def to_tensor(v6):
+    """[6, ...] tensor components (11,22,33,23,13,12) -> [3, 3, ...]."""
+    v6 = np.asarray(v6, dtype=np.float64)
+    t = np.zeros((3, 3) + v6.shape[1:])
+    for c, (i, j) in enumerate(PAIRS):
+        t[i, j] = v6[c]
+        t[j, i] = v6[c]
+    return t
+
+
+def to_comps(t):
+    """[3, 3, ...] symmetric tensor -> [6, ...] components."""
+    return np.stack([t[i, j] for (i, j) in PAIRS])
+
+
+# --------------------------------------------------------------------------
+# Grid, frequencies and the DFT pair (Section 2.3)
+# --------------------------------------------------------------------------
+def frequencies(N: int) -> np.ndarray:
+    """Index j in [0, N) -> frequency k in the reduced set -N/2 < k < N/2."""
+    j = np.arange(N)
+    return np.where(j <= (N - 1) // 2, j, j - N)
+
+
+def dft_forward(t):
+    """F: Fourier coefficients with the 1/|N| factor on the forward sum."""
+    N3 = np.prod(t.shape[-3:])
+    return np.fft.fftn(t, axes=(-3, -2, -1)) / N3
+
+
+def dft_inverse(th):
+    """F^-1: nodal values, no factor on the inverse sum."""
+    N3 = np.prod(th.shape[-3:])
+    return np.fft.ifftn(th, axes=(-3, -2, -1)) * N3
+
+
+def dft_forward_dense(t):
+    """Brute-force dense DFT of Eq. (DFT_forward_inverse)_1 (tiny grids only).
+
+    Entry [k, m] of each 1D matrix is exp(-2 pi i k m / N) with k the reduced
+    frequency stored at index j (k = j or j - N) and m the node index; the 3D
+    matrix is their Kronecker product. Used to pin `dft_forward`.
+    """
+    N1, N2, N3 = t.shape[-3:]
+    mats = []
+    for n in (N1, N2, N3):
+        k = frequencies(n)
+        m = np.arange(n)
+        mats.append(np.exp(-2j * np.pi * np.outer(k, m) / n))
+    M = np.kron(np.kron(mats[0], mats[1]), mats[2])
+    flat = t.reshape(t.shape[:-3] + (N1 * N2 * N3,))
+    out = flat @ M.T / (N1 * N2 * N3)
+    return out.reshape(t.shape[:-3] + (N1, N2, N3))
+
+
+# --------------------------------------------------------------------------
+# Projection operator (Appendix A)
+# --------------------------------------------------------------------------
+def ghat(xi):
+    """Ghat_ijlm(xi) of Eq. (FT_projection); xi [..., 3]; Ghat(0) = 0."""
+    xi = np.asarray(xi, dtype=np.float64)
+    n2 = np.sum(xi * xi, axis=-1)
+    zero = n2 == 0.0
+    n2s = np.where(zero, 1.0, n2)
+    d = I2
+    t = (np.einsum("...i,jl,...m->...ijlm", xi, d, xi)
+         + np.einsum("...i,jm,...l->...ijlm", xi, d, xi)
+         + np.einsum("...j,il,...m->...ijlm", xi, d, xi)
+         + np.einsum("...j,im,...l->...ijlm", xi, d, xi))
+    g = 0.5 * t / n2s[..., None, None, None, None]
+    g -= (np.einsum("...i,...j,...l,...m->...ijlm", xi, xi, xi, xi)
+          / (n2s ** 2)[..., None, None, None, None])
+    g[zero] = 0.0
+    return g
+
+
+def gamma_ref(xi, Cref):
+    """Gamma^ref_ijlm(xi) of Eq. (Gamma_explicit) via the acoustic tensor.
+
+    A_il = C_ijlm xi_j xi_m; Gamma = 1/4 (A^-1_jm xi_i xi_l + A^-1_jl xi_i xi_m
+    + A^-1_im xi_j xi_l + A^-1_il xi_j xi_m); Gamma(0) = 0.
+    """
+    xi = np.asarray(xi, dtype=np.float64)
+    n2 = np.sum(xi * xi, axis=-1)
+    zero = n2 == 0.0
+    xs = np.where(zero[..., None], 1.0, xi)
+    A = np.einsum("ijlm,...j,...m->...il", Cref, xs, xs)
+    Ai = np.linalg.inv(A)
+    g = 0.25 * (np.einsum("...jm,...i,...l->...ijlm", Ai, xs, xs)
+                + np.einsum("...jl,...i,...m->...ijlm", Ai, xs, xs)
+                + np.einsum("...im,...j,...l->...ijlm", Ai, xs, xs)
+                + np.einsum("...il,...j,...m->...ijlm", Ai, xs, xs))
+    g[zero] = 0.0
+    return g
+
+
+def project(tau):
+    """G tau = F^-1 [Ghat : F[tau]] for a real field tau [3, 3, N, N, N].
+
+    Eq. (discrete_projection). Ghat is evaluated one k1-slice at a time so
+    that large grids fit in memory; no other reordering. The imaginary part
+    left by the inverse transform must vanish (G is a real matrix); it is
+    checked and dropped.
+    """
+    N1, N2, N3 = tau.shape[-3:]
+    th = dft_forward(tau)
+    out = np.empty_like(th)
+    k2 = frequencies(N2)
+    k3 = frequencies(N3)
+    for a, k1 in enumerate(frequencies(N1)):
+        xi = np.stack(np.broadcast_arrays(np.float64(k1), k2[:, None] * 1.0,
+                                          k3[None, :] * 1.0), axis=-1)
+        g = ghat(xi)  # [N2, N3, 3, 3, 3, 3]
+        out[:, :, a] = np.einsum("bcijlm,lmbc->ijbc", g, th[:, :, a])
+    res = dft_inverse(out)
+    scale = max(np.abs(tau).max(), 1e-300)
+    assert np.abs(res.imag).max() <= 1e-12 * scale, "G tau not real"
+    return res.real
+
+
+def inner(a, b) -> float:
+    """Double contraction summed over nodes, Eq. (trapz) without the weight."""
+    return float(np.sum(a * b))
+
+
+# --------------------------------------------------------------------------
+# J2 elasto-plasticity with linear hardening (Section 4.2, n = 1)
+# --------------------------------------------------------------------------
+@dataclass
+class J2Result:
+    sigma: np.ndarray        # [3, 3, ...]
+    eps_p: np.ndarray        # [3, 3, ...] trial (updated) plastic strain
+    epbar: np.ndarray        # [...] trial accumulated plastic strain
+    plastic: np.ndarray      # [...] bool
+    dgamma: np.ndarray       # [...]
+    seq_tr: np.ndarray       # [...] trial von Mises stress
+    Ntr: np.ndarray          # [3, 3, ...] trial flow direction
+    K: np.ndarray
+    G: np.ndarray
+    H: np.ndarray
+
+
+def material_fields(phase, mats):
+    """Per-voxel (K, G, sigma_y, H) arrays from a phase map."""
+    tab = np.array([m.as_tuple() if hasattr(m, "as_tuple") else tuple(m)
+                    for m in mats], dtype=np.float64)
+    ph = np.asarray(phase).astype(np.int64)
+    return tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3]
+
+
+def j2_update(eps, eps_p_t, epbar_t, K, G, sy, H, tie=1e-12):
+    """Backward-Euler elastic predictor / plastic corrector.
+
+    eps, eps_p_t: [3, 3, ...]; epbar_t, K, G, sy, H: [...].
+    Trial state (Eq. model:plas:trial), elastic branch (Eq. model:plas:elas),
+    closed-form return for n = 1: dgamma = Phi_tr / (3G + H), update
+    (Eq. model:plas:corrector).
+    """
+    ee = eps - eps_p_t
+    tr = ee[0, 0] + ee[1, 1] + ee[2, 2]
+    dev = ee - tr / 3.0 * I2.reshape(3, 3, *([1] * (ee.ndim - 2)))
+    sig_tr = K * tr * I2.reshape(3, 3, *([1] * (ee.ndim - 2))) + 2.0 * G * dev
+    s = sig_tr - (sig_tr[0, 0] + sig_tr[1, 1] + sig_tr[2, 2]) / 3.0 * \
+        I2.reshape(3, 3, *([1] * (ee.ndim - 2)))
+    seq = np.sqrt(1.5 * np.sum(s * s, axis=(0, 1)))
+    phi = seq - (sy + H * epbar_t)
+    plastic = phi > tie * sy
+    seq_safe = np.where(seq > 0.0, seq, 1.0)
+    Ntr = 1.5 * s / seq_safe
+    dgamma = np.where(plastic, phi / (3.0 * G + H), 0.0)
+    eps_p = eps_p_t + dgamma * Ntr
+    epbar = epbar_t + dgamma
+    ee2 = eps - eps_p
+    tr2 = ee2[0, 0] + ee2[1, 1] + ee2[2, 2]
+    dev2 = ee2 - tr2 / 3.0 * I2.reshape(3, 3, *([1] * (ee.ndim - 2)))
+    sigma = K * tr2 * I2.reshape(3, 3, *([1] * (ee.ndim - 2))) + 2.0 * G * dev2
+    return J2Result(sigma, eps_p, epbar, plastic, dgamma, seq, Ntr, K, G, H)
+
+
+def j2_tangent(res: J2Result, sl=slice(None)):
+    """Consistent tangent C_ijlm, [3, 3, 3, 3, M] for the voxels in `sl`.
+
+    Elastic: C = C_e = K I(x)I + 2G I_d. Plastic:
+    C = C_e - 6 G^2 dgamma / seq_tr I_d + 4 G^2 (dgamma / seq_tr - 1/(3G + H)) N(x)N.
+    """
+    K = res.K.reshape(-1)[sl]
+    G = res.G.reshape(-1)[sl]
+    H = res.H.reshape(-1)[sl]
+    dg = res.dgamma.reshape(-1)[sl]
+    seq = res.seq_tr.reshape(-1)[sl]
+    pl = res.plastic.reshape(-1)[sl]
+    Nt = res.Ntr.reshape(3, 3, -1)[:, :, sl]
+    C = (np.einsum("ijlm,v->ijlmv", II, K)
+         + np.einsum("ijlm,v->ijlmv", I4d, 2.0 * G))
+    seqs = np.where(seq > 0.0, seq, 1.0)
+    a = np.where(pl, 6.0 * G * G * dg / seqs, 0.0)
+    b = np.where(pl, 4.0 * G * G * (dg / seqs - 1.0 / (3.0 * G + H)), 0.0)
+    C -= np.einsum("ijlm,v->ijlmv", I4d, a)
+    C += np.einsum("ijv,lmv,v->ijlmv", Nt, Nt, b)
+    return C
+
+
+class Tangent:
+    """The block-diagonal tangent D of Eq. (local_tangent), applied chunk-wise."""
+
+    CHUNK = 1 << 16
+
+    def __init__(self, res: J2Result):
+        self.res = res
+        self.shape = res.sigma.shape[2:]
+        self.V = int(np.prod(self.shape))
+
+    def apply(self, p):
+        """C : p for a field p [3, 3, N, N, N]."""
+        pf = p.reshape(3, 3, -1)
+        out = np.empty_like(pf)
+        for s in range(0, self.V, self.CHUNK):
+            sl = slice(s, min(s + self.CHUNK, self.V))
+            C = j2_tangent(self.res, sl)
+            out[:, :, sl] = np.einsum("ijlmv,lmv->ijv", C, pf[:, :, sl])
+        return out.reshape(p.shape)
+
+
+# --------------------------------------------------------------------------
+# Linear solve (Eq. linear_system) by conjugate gradients
+# --------------------------------------------------------------------------
+def matvec(tangent: Tangent, p):
+    """G (C : p) for a compatible field p."""
+    return project(tangent.apply(p))
+
+
+def cg(apply_A, b, tol, max_iter=2000, fixed_iters=None, floor=0.0):
+    """Hestenes-Stiefel CG with x_0 = 0 on A x = b, A = G C on E_N.
+
+    Stops when ||r_j|| <= max(tol ||r_0||, floor) (recursive residual) or,
+    if fixed_iters is given, after exactly that many iterations.
+    Returns (x, iterations, final relative residual).
+    """
+    x = np.zeros_like(b)
+    r = b.copy()
+    rr = inner(r, r)
+    rr0 = rr
+    if rr0 == 0.0:
+        return x, 0, 0.0
+    stop2 = max(tol * tol * rr0, floor * floor)
+    p = r.copy()
+    it = 0
+    while True:
+        if fixed_iters is None:
+            if rr <= stop2 or it >= max_iter:
+                break
+        elif it >= fixed_iters:
+            break
+        q = apply_A(p)
+        alpha = rr / inner(p, q)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = inner(r, r)
+        beta = rr_new / rr
+        rr = rr_new
+        p = r + beta * p
+        it += 1
+    return x, it, float(np.sqrt(rr / rr0))
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1: incremental-iterative Newton-CG
+# --------------------------------------------------------------------------
+@dataclass
+class State:
+    N: int
+    phase: np.ndarray
+    mats: tuple
+    E: np.ndarray = field(default=None)          # [3, 3]
+    eps_star: np.ndarray = field(default=None)   # [3, 3, N, N, N]
+    eps_p: np.ndarray = field(default=None)      # committed history
+    epbar: np.ndarray = field(default=None)
+
+    def __post_init__(self):
+        N = self.N
+        self.K, self.G, self.sy, self.H = material_fields(self.phase, self.mats)
+        if self.E is None:
+            self.E = np.zeros((3, 3))
+        if self.eps_star is None:
+            self.eps_star = np.zeros((3, 3, N, N, N))
+        if self.eps_p is None:
+            self.eps_p = np.zeros((3, 3, N, N, N))
+        if self.epbar is None:
+            self.epbar = np.zeros((N, N, N))
+
+    def constitutive(self, E, eps_star):
+        eps = eps_star + E[:, :, None, None, None]
+        return j2_update(eps, self.eps_p, self.epbar, self.K, self.G, self.sy, self.H)
+
+
+@dataclass
+class StepResult:
+    sigma: np.ndarray            # homogenised stress, 6 comps
+    newton_iters: int
+    cg_iters: int
+    cg_per_newton: list
+    residuals: list              # ||G sigma_i|| / ||sigma_i|| per Newton iteration
+    newton_norms: list           # ||de_i|| / ||E||_field per Newton iteration
+    converged: bool
+
+
+def solve_increment(st: State, dE6, tol_newton, tol_cg, max_newton=50,
+                    max_cg=2000, fixed_cg=None, fixed_newton=None):
+    """One increment of Algorithm 1 (increment loop body).
+
+    E_t+dt = E_t + dE; Newton on G sigma(E + eps*) = 0 starting from the
+    previous eps*; each Newton iteration solves G C de = -G sigma by CG;
+    then one final constitutive call at the converged strain gives the
+    homogenised stress (mean of the nodal stress, Eq. trapz) and the
+    committed history. Updates `st` in place.
+    """
+    E = st.E + to_tensor(np.asarray(dE6, dtype=np.float64))
+    eps_star = st.eps_star.copy()
+    V = st.N ** 3
+    normE = np.sqrt(V * np.sum(E * E))
+    it = 0
+    cg_total = 0
+    cg_list, res_list, nn_list = [], [], []
+    converged = False
+    while True:
+        res = st.constitutive(E, eps_star)
+        Gs = project(res.sigma)
+        nG = np.sqrt(inner(Gs, Gs))
+        ns = np.sqrt(inner(res.sigma, res.sigma))
+        res_list.append(nG / ns if ns > 0 else 0.0)
+        tan = Tangent(res)
+        if nG <= ROUNDOFF_RHS * ns:
+            de, ncg = np.zeros_like(Gs), 0
+        else:
+            de, ncg, _ = cg(lambda p: matvec(tan, p), -Gs, tol_cg, max_cg,
+                            fixed_iters=fixed_cg, floor=ROUNDOFF_RHS * ns)
+        eps_star += de
+        it += 1
+        cg_total += ncg
+        cg_list.append(ncg)
+        nde = np.sqrt(inner(de, de))
+        rel = nde / normE if normE > 0 else (0.0 if nde == 0 else np.inf)
+        nn_list.append(rel)
+        if fixed_newton is not None:
+            if it >= fixed_newton:
+                converged = True
+                break
+            continue
+        if rel <= tol_newton or nde == 0.0:
+            converged = True
+            break
+        if it >= max_newton:
+            break
+    res = st.constitutive(E, eps_star)
+    Sigma = to_comps(res.sigma.reshape(3, 3, -1).mean(axis=-1))
+    if converged:
+        st.E = E
+        st.eps_star = eps_star
+        st.eps_p = res.eps_p
+        st.epbar = res.epbar
+    return StepResult(Sigma, it, cg_total, cg_list, res_list, nn_list, converged)
+
+
+def macro_tangent(st: State, tol_cg, max_cg=2000):
+    """6x6 algorithmic macroscopic tangent dSigma/dE at the committed state.
+
+    Not in the paper. Column j perturbs tensor component j (a shear perturbs
+    (i,j) and (j,i) together by 1): b_j = -G (C : E_j), solve G C de_j = b_j,
+    C_hom[:, j] = mean(C : (E_j + de_j)). C is the tangent at the committed
+    strain with the history of the previous increment (the trial state that
+    produced the committed one), i.e. the last tangent of the increment.
+    Requires `st.last_res`, which `solve_increment_keep` sets.
+    """
+    res = st.last_res
+    tan = Tangent(res)
+    N = st.N
+    Ch = np.zeros((6, 6))
+    for j, (a, b) in enumerate(PAIRS):
+        Ej = np.zeros((3, 3))
+        Ej[a, b] = 1.0
+        Ej[b, a] = 1.0
+        Ef = np.broadcast_to(Ej[:, :, None, None, None], (3, 3, N, N, N)).copy()
+        CE = tan.apply(Ef)
+        rhs = -project(CE)
+        de, _, _ = cg(lambda p: matvec(tan, p), rhs, tol_cg, max_cg,
+                      floor=ROUNDOFF_RHS * np.sqrt(inner(CE, CE)))
+        s = tan.apply(Ef + de)
+        Ch[:, j] = to_comps(s.reshape(3, 3, -1).mean(axis=-1))
+    return Ch
+
+
+def solve_increment_keep(st: State, dE6, tol_newton, tol_cg, **kw):
+    """`solve_increment` that also keeps the final constitutive result.
+
+    The last constitutive call is evaluated against the history of the
+    previous increment, so it must be taken before the commit overwrites it.
+    """
+    eps_p_prev, epbar_prev = st.eps_p.copy(), st.epbar.copy()
+    r = solve_increment(st, dE6, tol_newton, tol_cg, **kw)
+    tmp = State(st.N, st.phase, st.mats, E=st.E, eps_star=st.eps_star,
+                eps_p=eps_p_prev, epbar=epbar_prev)
+    st.last_res = tmp.constitutive(st.E, st.eps_star)
+    return r
