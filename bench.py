@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT-Galerkin Newton-CG solver on one or more GB300s.
+
+Workload: the 243^3 periodic cell with random hard spheres (radii 3-8,
+hard fraction 0.2), J2 with linear hardening, uniaxial strain E11 ramped
+in increments of 0.0015, mixed precision (FP32 inner CG, FP64 return
+mapping, residual and homogenisation). One step = one load increment
+(Newton-CG to 1e-5 / CG 1e-8, floor 1e-6 in FP32) followed by the 6x6
+macroscopic tangent (six right-hand sides in one batched CG): the call pair
+an FE^2 macro solver makes per Gauss point. The warm-up increments take the
+cell past first yield, so the timed increments are plastic.
+
+Metric: CG-iteration voxels/s = N^3 x (CG iterations of the Newton solves +
+CG iterations of the six tangent solves) / time.
+
+With --gpus N under torchrun each rank solves its own cell (own seed): the
+path shards by cell with no data exchange (replicas; weak scaling).
+`--impl reference` times the FP64 numpy oracle on the host instead.
+"""
+import os
+
+# the oracle legs must use one host thread (counted as `cores`)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG-iter voxels/s at 243^3 (FP32-inner mixed precision)"
+UNIT = "voxel-iterations/s"
+
+# Algorithmic bytes per voxel and per field of each kernel kind (what the
+# kernel must read and write given its interface; FP32 fields are 24 B per
+# voxel, the half spectrum 6 x (H/N) x 8 B, the compact tangent 28 B).
+def bytes_per_voxel(N):
+    H = (N + 1) // 2
+    s32 = 6 * 8 * H / N
+    s64 = 2 * s32
+    return {
+        "p1_cg_f32": 24 + 24 + 24 + 28 + s32,      # r, p in; p out; tangent; spectrum out
+        "p2_f32": 2 * s32, "p3_f32": 2 * s32, "p4_f32": 2 * s32,
+        "p5_dot_f32": s32 + 24 + 24,               # spectrum in; q out; p in
+        "cg_update_f32": 4 * 24 + 2 * 24,          # x, p, r, q in; x, r out
+        "p1_tanrhs_f32": 28 + s32,
+        "p5_rhs_f32_to_f32": s32 + 24,
+        "p1_plain_f64": 48 + s64, "p2_f64": 2 * s64, "p3_f64": 2 * s64, "p4_f64": 2 * s64,
+        "p5_rhs_f64_to_f32": s64 + 24,
+    }
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--N", type=int, default=243)
+    ap.add_argument("--no-tangent", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- oracle legs
+def oracle_sample(N_full, seed, n_iters, sub=81):
+    """Time `n_iters` oracle CG iterations on the sub x sub x sub corner of the
+    same microstructure (periodic closure), after one constitutive
+    evaluation at the macroscopic strain the timed GPU increments start from
+    (E11 = 0.0045, zero history, eps* = 0). Returns (voxel-iterations/s, desc)."""
+    from oracle import fftg_oracle as O
+    from paper_1601_05970_gb300 import inputs as I
+    w = I.workload("spheres243" if N_full == 243 else "spheres135", seed=seed)
+    ph = np.ascontiguousarray(w["phase"][:sub, :sub, :sub])
+    st = O.State(sub, ph, w["mats"])
+    E = O.to_tensor(np.array([0.0045, 0, 0, 0, 0, 0]))
+    res = st.constitutive(E, np.zeros((3, 3, sub, sub, sub)))
+    tan = O.Tangent(res)
+    b = -O.project(res.sigma)
+    t0 = time.perf_counter()
+    O.cg(lambda p: O.matvec(tan, p), b, 1e-30, fixed_iters=n_iters)
+    dt = time.perf_counter() - t0
+    desc = (f"FP64 numpy oracle, {n_iters} CG iterations (G C p on full 3x3 tensors) on the "
+            f"{sub}^3 corner of the {N_full}^3 microstructure (seed {seed}), 1 host thread")
+    return sub ** 3 * n_iters / dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, desc = oracle_sample(args.N, 2, 1)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    ms = 1e3 * (81 ** 3) / value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"spheres{args.N}-uniaxial (oracle sample)", "N": args.N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- GPU leg
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1601_05970_gb300 import build, fftg
+    from paper_1601_05970_gb300 import inputs as I
+    build.build()
+    fftg.load()
+
+    N = args.N
+    w = I.workload("spheres243" if N == 243 else "spheres135", seed=2 + 1000 * rank)
+    dE = np.array([0.0015, 0, 0, 0, 0, 0]) if N == 243 else np.array([0, 0, 0, 0, 0, 0.001])
+    tol_nw, tol_cg = w["tol_newton"], w["tol_cg"]
+    cell = fftg.Cell(N, w["phase"], w["mats"], precision=args.precision,
+                     nrhs_tangent=0 if args.no_tangent else 6)
+    stream = cell.stream
+    V = N ** 3
+
+    def one_step(acc):
+        sig, nn, nc = cell.step(dE, tol_nw, tol_cg)
+        acc["newton"] += nn
+        acc["cg"] += nc
+        if not args.no_tangent:
+            C, nt = cell.tangent(tol_cg)
+            acc["tangent_cg"] += nt
+            acc["tangent_calls"] += 1
+        acc["sigma"] = sig
+
+    warm = dict(newton=0, cg=0, tangent_cg=0, tangent_calls=0)
+    for _ in range(args.warmup):
+        one_step(warm)
+    cell.profile(True)
+    cell.profile_reset()
+    acc = dict(newton=0, cg=0, tangent_cg=0, tangent_calls=0)
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = cell.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step(acc)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if not args.no_clocks else None
+    launches = cell.launch_count() - launches0
+    dev_ms = ev0.elapsed_time(ev1)
+    wall_ms = 1e3 * (t1 - t0)
+    prof = cell.profile_read()
+    field_iters = acc["cg"] + acc["tangent_cg"]
+    units = float(V) * field_iters
+    if dist:
+        t = torch.tensor([dev_ms, wall_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units, float(launches)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dev_ms, wall_ms = float(t[0]), float(t[1])
+        units, launches = float(u[0]), int(u[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    bpv = bytes_per_voxel(N)
+    kind, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
+    # effective field-launches of the CG kernels = CG field-iterations
+    # (chunked launches past convergence return at entry and do no work)
+    eff = {"p1_cg_f32": field_iters, "p5_dot_f32": field_iters, "cg_update_f32": field_iters,
+           "p2_f32": field_iters + 6 * acc["tangent_calls"],
+           "p3_f32": field_iters + 6 * acc["tangent_calls"],
+           "p4_f32": field_iters + 6 * acc["tangent_calls"]}
+    hbm, peak_kind = measured_hbm()
+    roof = None
+    if kind in bpv and kind in eff:
+        alg_bytes = eff[kind] * V * bpv[kind]
+        achieved = alg_bytes / (kms * 1e-3) / 1e9
+        per_launch = alg_bytes / max(eff[kind], 1)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": kind,
+                "peak_source": peak_kind, "bytes_per_launch": per_launch,
+                "avg_launch_ms": kms / max(eff[kind], 1)}
+    line = {
+        "metric": METRIC, "value": units / (dev_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"spheres{N}-uniaxial", "N": N, "voxels": V,
+                   "precision": args.precision, "hard_fraction": round(w["fraction"], 4),
+                   "seed": w["seed"], "step": "one load increment (Newton-CG) + 6x6 tangent"
+                   if not args.no_tangent else "one load increment (Newton-CG)",
+                   "l2": "inputs larger than L2 (each FP32 field 344 MB)" if N == 243
+                   else "inputs larger than L2 (each FP32 field 59 MB; spectra + fields > 129 MB)",
+                   "parallelism": f"replicas x{world}",
+                   "newton_iters": acc["newton"], "cg_iters": acc["cg"],
+                   "tangent_cg_iters": acc["tangent_cg"]},
+        "e2e": {"value": units / (wall_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 48,
+                "d2h_bytes_per_step": 48 + (288 if not args.no_tangent else 0)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clocks,
+        "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in sorted(
+            prof.items(), key=lambda kv: -kv[1][0])},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        v, desc = oracle_sample(N, w["seed"], 3)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

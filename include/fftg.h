@@ -1,0 +1,201 @@
+/*
+ * fftg: FFT-Galerkin Newton-CG solver for periodic small-strain J2
+ * micromechanics on one GB300 GPU (sm_103a).
+ *
+ * The method is that of Zeman, de Geus, Vondrejc, Peerlings and Geers,
+ * "A finite element perspective on non-linear FFT-based micromechanical
+ * simulations" (arXiv:1601.05970). A periodic cell of N^3 voxels (N odd,
+ * a product of 3s and 5s, 3 <= N <= 243) with a two- or more-phase
+ * microstructure is loaded by a macroscopic strain E; the library solves the
+ * nodal equilibrium G sigma(E + eps*) = 0 (Eq. nodal_equilibrium_equations)
+ * for the compatible fluctuation eps* by the incremental Newton-CG scheme of
+ * Algorithm 1, with the J2 elasto-plastic law of Section 4.2 (linear
+ * isotropic hardening), and returns the homogenised stress (Eq. trapz: the
+ * nodal mean of sigma).
+ *
+ * Conventions shared by every entry point:
+ *  - A symmetric tensor is 6 doubles in the order (11, 22, 33, 23, 13, 12),
+ *    tensor (not engineering, not Mandel) components.
+ *  - A field is [6][N][N][N] (component slowest, then x1, x2, x3 fastest);
+ *    a scalar field is [N][N][N].
+ *  - Return value: FFTG_OK (0) or a negative FFTG_E* code. On any error the
+ *    committed state (E, eps*, plastic history) is left as it was.
+ *  - The caller owns every host array; the library copies what it needs.
+ *    A handle owns (or borrows, see fftg_options.workspace) its device
+ *    memory. One handle is used from one host thread at a time.
+ *  - Device pointers (the fftg_op_* calls) are plain CUDA device addresses
+ *    on the handle's device, in the handle's stream order.
+ */
+#ifndef FFTG_H
+#define FFTG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define FFTG_OK               0
+#define FFTG_EINVAL          -1  /* bad argument: even N, N not 3^a 5^b, phase id, tolerance <= 0 */
+#define FFTG_ENOMEM          -2  /* device allocation failed or workspace too small */
+#define FFTG_ENOCONV_NEWTON  -3  /* Newton reached max_newton without meeting tol_newton */
+#define FFTG_ENOCONV_CG      -4  /* a CG solve reached max_cg without meeting its tolerance */
+#define FFTG_ENAN            -5  /* a residual or norm became NaN or Inf */
+#define FFTG_ECUDA           -6  /* a CUDA call failed */
+#define FFTG_ESTATE          -7  /* call out of order (e.g. tangent before any step) */
+
+/* ---------------------------------------------------------------- precision */
+#define FFTG_FP64   0  /* every step in FP64 */
+#define FFTG_MIXED  1  /* FP32 inner CG (FFT, projection, tangent contraction);
+                          FP64 return mapping, residual G sigma, Newton test and
+                          homogenised stress: Newton acts as iterative refinement */
+
+/* ---------------------------------------------------------------- fields */
+#define FFTG_FIELD_STRAIN  0  /* total strain E + eps*, [6][N^3] */
+#define FFTG_FIELD_STRESS  1  /* stress at the committed state, [6][N^3] */
+#define FFTG_FIELD_EPBAR   2  /* accumulated plastic strain, [N^3] */
+#define FFTG_FIELD_EPS_P   3  /* plastic strain tensor, [6][N^3] */
+
+typedef struct fftg_handle fftg_handle;
+
+/* One material phase: J2 plasticity with linear isotropic hardening,
+ * Section 4.2 with n = 1: C_e = K I(x)I + 2G I_d, yield function
+ * Phi = sigma_eq - (sigma_y + H epbar). A phase with sigma_y >= 1e300 is
+ * linear elastic. */
+typedef struct {
+    double K;        /* bulk modulus, > 0 */
+    double G;        /* shear modulus, > 0 */
+    double sigma_y;  /* initial yield stress sigma_0, > 0 */
+    double H;        /* linear hardening modulus, >= 0 */
+} fftg_phase;
+
+typedef struct {
+    int    precision;       /* FFTG_FP64 or FFTG_MIXED (default FFTG_MIXED) */
+    int    max_newton;      /* Newton iteration cap per increment (default 50) */
+    int    max_cg;          /* CG iteration cap per solve (default 2000) */
+    double cg_inner_floor;  /* FFTG_MIXED: the FP32 CG tolerance is
+                               max(tol_cg, cg_inner_floor) (default 1e-6) */
+    int    fixed_cg;        /* > 0: every CG solve runs exactly this many
+                               iterations (parity mode); 0 = off */
+    int    fixed_newton;    /* > 0: every increment runs exactly this many
+                               Newton iterations (parity mode); 0 = off */
+    void*  stream;          /* cudaStream_t the handle works in; NULL = the
+                               legacy default stream */
+    void*  workspace;       /* optional device memory of at least
+                               fftg_workspace_size() bytes, 256-byte aligned,
+                               owned by the caller and kept alive until
+                               fftg_destroy; NULL = the library allocates */
+    size_t workspace_bytes;
+    int    nrhs_tangent;    /* right-hand sides held for fftg_tangent: 0 (no
+                               tangent), or 6 (default 6) */
+} fftg_options;
+
+/* Per-increment diagnostics of the last fftg_step (Algorithm 1). */
+#define FFTG_MAX_NEWTON_LOG 64
+typedef struct {
+    int    status;                              /* return code of the step */
+    int    newton_iters;                        /* linear solves performed */
+    int    cg_iters;                            /* sum over the solves */
+    int    cg_per_newton[FFTG_MAX_NEWTON_LOG];
+    double newton_norm[FFTG_MAX_NEWTON_LOG];    /* ||d eps*|| / ||E||_field, Algorithm 1 Newton test */
+    double residual[FFTG_MAX_NEWTON_LOG];       /* ||G sigma|| / ||sigma|| (Table 3 analogue) */
+    double cg_relres[FFTG_MAX_NEWTON_LOG];      /* final recursive ||r||/||r0|| of each solve */
+} fftg_stats;
+
+/* Fill *opt with the defaults listed above. */
+void fftg_default_options(fftg_options* opt);
+
+/* Library version string. */
+const char* fftg_version(void);
+
+/* Device bytes a handle of this size needs (workspace for fftg_options). */
+int fftg_workspace_size(int N, const fftg_options* opt, size_t* bytes);
+
+/* Create a cell: validates N (odd 3^a 5^b, Section 2.3: odd grids give a
+ * conforming trigonometric space with no Nyquist mode), copies the phase
+ * map (uint8 [N][N][N], x1 slowest, values < nphase) and the nphase
+ * materials to the device, and zeroes E, eps* and the plastic history
+ * (Algorithm 1, initial conditions). */
+int fftg_create(fftg_handle** h, int N, const uint8_t* phase, int nphase,
+                const fftg_phase* mats, const fftg_options* opt);
+
+/* One load increment (Algorithm 1, one pass of the increment loop):
+ * E <- E + dE, Newton iterations on G sigma(E + eps*) = 0 starting from the
+ * previous eps* (Alg. 1 "initial guess for the next increment"), each
+ * solving G C d eps* = -G sigma (Eq. linear_system) by CG to the relative
+ * residual tol_cg (the CG test of Algorithm 1), until
+ * ||d eps*|| / ||E||_field <= tol_newton (its Newton test). Then the stress at the converged strain is homogenised into
+ * sigma_out[6] and the plastic history is committed.
+ * newton_iters / cg_iters may be NULL. On error nothing is committed. */
+int fftg_step(fftg_handle* h, const double dE[6], double tol_newton,
+              double tol_cg, double sigma_out[6], int* newton_iters,
+              int* cg_iters);
+
+/* Diagnostics of the last fftg_step. */
+int fftg_last_stats(fftg_handle* h, fftg_stats* out);
+
+/* 6x6 macroscopic algorithmic tangent dSigma/dE at the last converged
+ * increment (not in the paper; the quantity an FE^2 macro solver needs).
+ * Column j perturbs tensor component j (a shear perturbs (i,j) and (j,i)
+ * together by 1): the six right-hand sides -G(C : E_j) are solved in one
+ * batched CG with the consistent tangent C of the converged state, and
+ * C_out[i*6 + j] = mean(C : (E_j + d eps_j))_i. Row-major. */
+int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters);
+
+/* Checkpoint/restore of the committed state: E[6], eps*[6][V], eps_p[6][V],
+ * epbar[V] as FP64, in that order (fftg_state_bytes() bytes). */
+size_t fftg_state_bytes(const fftg_handle* h);
+int fftg_get_state(fftg_handle* h, void* host_buf, size_t bytes);
+int fftg_set_state(fftg_handle* h, const void* host_buf, size_t bytes);
+
+/* Copy a committed field to host memory (FFTG_FIELD_*; FP64). */
+int fftg_get_field(fftg_handle* h, int which, double* host_out);
+
+void fftg_destroy(fftg_handle* h);
+
+/* ---------------------------------------------------------------- operators
+ * The steps of the path on caller device buffers, for callers that drive
+ * their own iteration and for parity tests. All run in the handle's stream
+ * and return after enqueueing, except where a host output is written (then
+ * the stream is synchronised). `precision` selects FP64 (double buffers) or
+ * FP32 (float buffers) for the FFT-side operators. */
+
+/* out = G tau (Eq. discrete_projection) for a real field tau [6][N^3]:
+ * forward DFT, Ghat of Appendix A Eq. (FT_projection) at every frequency
+ * (Ghat(0) = 0), inverse DFT. tau and out may alias. */
+int fftg_op_project(fftg_handle* h, int precision, const void* tau_dev, void* out_dev);
+
+/* Evaluate the constitutive law at E_trial + eps where E_trial = E + dE
+ * (dE may be NULL) and eps [6][N^3] FP64 is a device field (NULL = the
+ * committed eps*), against the committed history: writes sigma [6][N^3]
+ * FP64 (may be NULL) and keeps the consistent tangent (Section 4.2) for
+ * fftg_op_matvec. */
+int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps_dev,
+                         double* sigma_dev);
+
+/* q = G (C : p) with the tangent of the last fftg_op_constitutive (or of
+ * the last converged increment), p and q [6][N^3] in `precision`; writes
+ * <p, q> (Frobenius, summed over voxels) to *pq when pq is not NULL. */
+int fftg_op_matvec(fftg_handle* h, int precision, const void* p_dev, void* q_dev,
+                   double* pq);
+
+/* ---------------------------------------------------------------- profiling
+ * Per-kernel timing of a handle's own launches with CUDA events recorded in
+ * its stream around every launch (off by default; a few microseconds per
+ * launch when on). Kernel kinds are numbered 0 .. fftg_profile_kinds()-1. */
+int fftg_profile_kinds(void);
+const char* fftg_profile_name(int kind);
+int fftg_profile_enable(fftg_handle* h, int on);
+int fftg_profile_reset(fftg_handle* h);
+/* Synchronises the stream; total device milliseconds and launches of `kind`
+ * since the last reset (or since profiling was enabled). */
+int fftg_profile_read(fftg_handle* h, int kind, double* total_ms, long long* launches);
+/* Kernels this handle has launched since creation (always counted). */
+long long fftg_launch_count(const fftg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTG_H */

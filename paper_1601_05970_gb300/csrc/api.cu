@@ -1,0 +1,897 @@
+// C-ABI of the fftg library: handle lifetime, the Newton-CG driver of
+// Algorithm 1 and the operator-level entry points. Everything numerical runs
+// in the kernels of passes.cuh and pointwise.cuh; the host only sequences
+// launches and reads a few scalars per Newton iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fftg.h"
+#include "passes.cuh"
+#include "pointwise.cuh"
+
+namespace fftg {
+#define FFTG_EXTERN_N(n) extern template cudaError_t run_pass_n<n>(PassKind, const PassArgs&, int, cudaStream_t);
+FFTG_EXTERN_N(3)
+FFTG_EXTERN_N(5)
+FFTG_EXTERN_N(9)
+FFTG_EXTERN_N(15)
+FFTG_EXTERN_N(25)
+FFTG_EXTERN_N(27)
+FFTG_EXTERN_N(45)
+FFTG_EXTERN_N(75)
+FFTG_EXTERN_N(81)
+FFTG_EXTERN_N(125)
+FFTG_EXTERN_N(135)
+FFTG_EXTERN_N(225)
+FFTG_EXTERN_N(243)
+#undef FFTG_EXTERN_N
+
+static bool supported_n(int N) {
+    switch (N) {
+        case 3: case 5: case 9: case 15: case 25: case 27: case 45: case 75: case 81: case 125:
+        case 135: case 225: case 243:
+            return true;
+        default:
+            return false;
+    }
+}
+
+cudaError_t run_pass(int N, PassKind kind, const PassArgs& a, int nf, cudaStream_t s) {
+    switch (N) {
+#define FFTG_CASE(n) case n: return run_pass_n<n>(kind, a, nf, s);
+        FFTG_CASE(3) FFTG_CASE(5) FFTG_CASE(9) FFTG_CASE(15) FFTG_CASE(25) FFTG_CASE(27)
+        FFTG_CASE(45) FFTG_CASE(75) FFTG_CASE(81) FFTG_CASE(125) FFTG_CASE(135) FFTG_CASE(225)
+        FFTG_CASE(243)
+#undef FFTG_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N>
+static int row_blocks_n(bool fp64) {
+    return fp64 ? Cfg<N, double>::row_blocks : Cfg<N, float>::row_blocks;
+}
+
+int row_blocks(int N, bool fp64) {
+    switch (N) {
+#define FFTG_CASE(n) case n: return row_blocks_n<n>(fp64);
+        FFTG_CASE(3) FFTG_CASE(5) FFTG_CASE(9) FFTG_CASE(15) FFTG_CASE(25) FFTG_CASE(27)
+        FFTG_CASE(45) FFTG_CASE(75) FFTG_CASE(81) FFTG_CASE(125) FFTG_CASE(135) FFTG_CASE(225)
+        FFTG_CASE(243)
+#undef FFTG_CASE
+        default: return 0;
+    }
+}
+}  // namespace fftg
+
+using namespace fftg;
+
+namespace {
+enum : int {
+    KK_CONSTITUTIVE_F32 = PK_COUNT, KK_CONSTITUTIVE_F64, KK_CG_UPDATE_F32, KK_CG_UPDATE_F64,
+    KK_NEWTON_UPDATE_F32, KK_NEWTON_UPDATE_F64, KK_TANGENT_FLOOR, KK_TANGENT_AVERAGE, KK_COUNT
+};
+const char* const kKindNames[KK_COUNT] = {
+    "p1_plain_f64", "p1_plain_f32", "p1_tan_f64", "p1_tan_f32", "p1_cg_f64", "p1_cg_f32",
+    "p1_tanrhs_f64", "p1_tanrhs_f32", "p2_f64", "p2_f32", "p4_f64", "p4_f32", "p3_f64", "p3_f32",
+    "p5_plain_f64", "p5_plain_f32", "p5_dot_f64", "p5_dot_f32", "p5_rhs_f64_to_f64",
+    "p5_rhs_f64_to_f32", "p5_rhs_f32_to_f32", "constitutive_f32", "constitutive_f64",
+    "cg_update_f32", "cg_update_f64", "newton_update_f32", "newton_update_f64", "tangent_floor",
+    "tangent_average"};
+
+// Ring of event pairs around the handle's launches; drained at every read.
+struct Prof {
+    static constexpr int kRing = 4096;
+    bool on = false;
+    cudaEvent_t ev0[kRing] = {}, ev1[kRing] = {};
+    int kind[kRing] = {};
+    int n = 0;
+    double ms[KK_COUNT] = {};
+    long long cnt[KK_COUNT] = {};
+};
+}  // namespace
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            h->last_cuda = e_;                     \
+            return FFTG_ECUDA;                     \
+        }                                          \
+    } while (0)
+
+struct fftg_handle {
+    int N = 0;
+    long long V = 0;
+    int H = 0;
+    int mixed = 1;
+    int nrhs = 6;
+    fftg_options opt{};
+    cudaStream_t stream = nullptr;
+    cudaError_t last_cuda = cudaSuccess;
+    bool own_ws = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+
+    uint8_t* phase = nullptr;
+    double* mats = nullptr;
+    int nphase = 0;
+    double* eps_star = nullptr;  // committed
+    double* eps_work = nullptr;  // working copy during an increment
+    double* eps_p[2] = {nullptr, nullptr};
+    double* epbar[2] = {nullptr, nullptr};
+    int hist = 0;                // index of the committed history
+    double* sigma = nullptr;
+    void* tangent = nullptr;     // [7][V] inner precision
+    void* x = nullptr;
+    void* r = nullptr;
+    void* p = nullptr;
+    void* q = nullptr;
+    void* spec = nullptr;
+    void* tw32 = nullptr;
+    void* tw64 = nullptr;
+    double* partials = nullptr;
+    CGState* cg = nullptr;       // [6]
+    NewtonDev* nd = nullptr;
+    double* out36 = nullptr;
+
+    CGState* h_cg = nullptr;     // pinned mirrors
+    NewtonDev* h_nd = nullptr;
+    double* h_out36 = nullptr;
+
+    double E[6] = {0, 0, 0, 0, 0, 0};
+    bool have_tangent = false;
+    fftg_stats stats{};
+    long long launches = 0;
+    Prof* prof = nullptr;
+};
+
+// Drain the recorded event pairs into the per-kind totals.
+static cudaError_t prof_drain(fftg_handle* h) {
+    Prof* P = h->prof;
+    if (!P || P->n == 0) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(P->ev1[P->n - 1]);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < P->n; ++i) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, P->ev0[i], P->ev1[i]);
+        if (e != cudaSuccess) return e;
+        P->ms[P->kind[i]] += t;
+        P->cnt[P->kind[i]] += 1;
+    }
+    P->n = 0;
+    return cudaSuccess;
+}
+
+// Bracket one launch: returns the slot to close, or -1 when profiling is off.
+static int prof_begin(fftg_handle* h, int kind) {
+    ++h->launches;
+    Prof* P = h->prof;
+    if (!P || !P->on) return -1;
+    if (P->n == Prof::kRing && prof_drain(h) != cudaSuccess) return -1;
+    const int i = P->n++;
+    P->kind[i] = kind;
+    cudaEventRecord(P->ev0[i], h->stream);
+    return i;
+}
+
+static void prof_end(fftg_handle* h, int slot) {
+    if (slot >= 0) cudaEventRecord(h->prof->ev1[slot], h->stream);
+}
+
+// One pass launch, instrumented.
+static cudaError_t pass(fftg_handle* h, PassKind kind, const PassArgs& a, int nf) {
+    const int slot = prof_begin(h, kind);
+    cudaError_t e = run_pass(h->N, kind, a, nf, h->stream);
+    prof_end(h, slot);
+    return e;
+}
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p0, off_eps_p1, off_epbar0,
+        off_epbar1, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32, off_tw64,
+        off_partials, off_cg, off_nd, off_out36, total;
+};
+
+Layout make_layout(int N, int mixed, int nrhs) {
+    const size_t V = (size_t)N * N * N;
+    const size_t H = (size_t)(N + 1) / 2;
+    const size_t ts = mixed ? 4 : 8;
+    const size_t nf = (size_t)std::max(1, nrhs);
+    const size_t spec64 = 6 * (size_t)N * N * H * 16;
+    const size_t specT = nf * 6 * (size_t)N * N * H * (2 * ts);
+    const size_t rb = (size_t)std::max(fftg::row_blocks(N, true), fftg::row_blocks(N, false));
+    const size_t npart = std::max((size_t)kMaxPointwiseBlocks * 36, rb * 2 * 6);
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    L.off_phase = take(V);
+    L.off_mats = take(256 * 4 * 8);
+    L.off_eps_star = take(6 * V * 8);
+    L.off_eps_work = take(6 * V * 8);
+    L.off_eps_p0 = take(6 * V * 8);
+    L.off_eps_p1 = take(6 * V * 8);
+    L.off_epbar0 = take(V * 8);
+    L.off_epbar1 = take(V * 8);
+    L.off_sigma = take(6 * V * 8);
+    L.off_tangent = take(7 * V * ts);
+    L.off_x = take(nf * 6 * V * ts);
+    L.off_r = take(nf * 6 * V * ts);
+    L.off_p = take(nf * 6 * V * ts);
+    L.off_q = take(nf * 6 * V * ts);
+    L.off_spec = take(std::max(spec64, specT));
+    L.off_tw32 = take((size_t)N * 8);
+    L.off_tw64 = take((size_t)N * 16);
+    L.off_partials = take(npart * 8);
+    L.off_cg = take(6 * sizeof(CGState));
+    L.off_nd = take(sizeof(NewtonDev));
+    L.off_out36 = take(36 * 8);
+    L.total = o;
+    return L;
+}
+
+bool valid_grid(int N) {
+    if (N < 3 || N % 2 == 0) return false;
+    int m = N;
+    while (m % 3 == 0) m /= 3;
+    while (m % 5 == 0) m /= 5;
+    return m == 1 && fftg::supported_n(N);
+}
+
+double frob6(const double* v) {
+    return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] +
+                     2.0 * (v[3] * v[3] + v[4] * v[4] + v[5] * v[5]));
+}
+
+// w_N^j = exp(-2 pi i j / N), evaluated in long double on the host.
+void twiddles(int N, double* tw64, float* tw32) {
+    const long double two_pi = 6.283185307179586476925286766559L;
+    for (int j = 0; j < N; ++j) {
+        const long double a = two_pi * (long double)j / (long double)N;
+        const double c = (double)cosl(a), s = (double)-sinl(a);
+        tw64[2 * j] = c;
+        tw64[2 * j + 1] = s;
+        tw32[2 * j] = (float)c;
+        tw32[2 * j + 1] = (float)s;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- internals
+static int sync_read(fftg_handle* h, bool cg_all, bool nd) {
+    if (cg_all) CK(cudaMemcpyAsync(h->h_cg, h->cg, 6 * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+    if (nd) CK(cudaMemcpyAsync(h->h_nd, h->nd, sizeof(NewtonDev), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FFTG_OK;
+}
+
+static int launch_constitutive(fftg_handle* h, const double E[6], const double* eps, double* sigma,
+                               bool write_history, CGState* cg, bool write_tangent = true) {
+    ConstArgs a{};
+    a.V = h->V;
+    for (int c = 0; c < 6; ++c) a.E[c] = E[c];
+    a.eps = eps;
+    a.eps_p = h->eps_p[h->hist];
+    a.epbar = h->epbar[h->hist];
+    a.phase = h->phase;
+    a.mats = h->mats;
+    a.sigma = sigma;
+    a.eps_p_new = write_history ? h->eps_p[1 - h->hist] : nullptr;
+    a.epbar_new = write_history ? h->epbar[1 - h->hist] : nullptr;
+    a.tangent = write_tangent ? h->tangent : nullptr;
+    a.partials = h->partials;
+    a.nd = h->nd;
+    a.cg = cg;
+    a.tie = 1e-12;
+    const int nb = pointwise_blocks(h->V);
+    const int slot = prof_begin(h, h->mixed ? KK_CONSTITUTIVE_F32 : KK_CONSTITUTIVE_F64);
+    if (h->mixed)
+        k_constitutive<float><<<nb, kThreads, 0, h->stream>>>(a);
+    else
+        k_constitutive<double><<<nb, kThreads, 0, h->stream>>>(a);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    return FFTG_OK;
+}
+
+static PassArgs base_args(fftg_handle* h, bool fp64) {
+    PassArgs a{};
+    a.tw = fp64 ? h->tw64 : h->tw32;
+    a.partials = h->partials;
+    a.fstride = 6 * h->V;
+    a.sstride = 6LL * h->N * h->N * h->H;
+    a.tstride = 0;
+    return a;
+}
+
+// Forward-project-inverse core on the spectrum buffer (P2, P3, P4).
+static int run_p234(fftg_handle* h, bool fp64, double scale, CGState* cg, int nf) {
+    PassArgs a = base_args(h, fp64);
+    a.out = h->spec;
+    a.cg = cg;
+    a.scale = scale;
+    CK(pass(h, fp64 ? PK_P2_F64 : PK_P2_F32, a, nf));
+    CK(pass(h, fp64 ? PK_P3_F64 : PK_P3_F32, a, nf));
+    CK(pass(h, fp64 ? PK_P4_F64 : PK_P4_F32, a, nf));
+    return FFTG_OK;
+}
+
+// r = -G sigma (FP64 FFT), rounded to the inner precision; x = 0.
+static int launch_residual(fftg_handle* h) {
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    PassArgs a = base_args(h, true);
+    a.in = h->sigma;
+    a.out = h->spec;
+    CK(pass(h, PK_P1_PLAIN_F64, a, 1));
+    int rc = run_p234(h, true, -invN3, nullptr, 1);
+    if (rc) return rc;
+    PassArgs b = base_args(h, true);
+    b.in = h->spec;
+    b.out = h->r;
+    b.cg = h->cg;
+    CK(pass(h, h->mixed ? PK_P5_RHS_F64_TO_F32 : PK_P5_RHS_F64_TO_F64, b, 1));
+    CK(cudaMemsetAsync(h->x, 0, 6 * h->V * (h->mixed ? 4 : 8), h->stream));
+    return FFTG_OK;
+}
+
+// One CG iteration on nf fields: the fused matvec passes and the update.
+static int launch_cg_iteration(fftg_handle* h, int nf) {
+    const bool f64 = !h->mixed;
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    PassArgs a = base_args(h, f64);
+    a.aux = h->r;
+    a.aux2 = h->p;
+    a.tangent = h->tangent;
+    a.out = h->spec;
+    a.cg = h->cg;
+    CK(pass(h, f64 ? PK_P1_CG_F64 : PK_P1_CG_F32, a, nf));
+    int rc = run_p234(h, f64, invN3, h->cg, nf);
+    if (rc) return rc;
+    PassArgs b = base_args(h, f64);
+    b.in = h->spec;
+    b.out = h->q;
+    b.aux = h->p;
+    b.cg = h->cg;
+    CK(pass(h, f64 ? PK_P5_DOT_F64 : PK_P5_DOT_F32, b, nf));
+    VecArgs u{};
+    u.V = h->V;
+    u.x = h->x;
+    u.r = h->r;
+    u.p = h->p;
+    u.q = h->q;
+    u.cg = h->cg;
+    u.partials = h->partials;
+    u.fstride = 6 * h->V;
+    dim3 g(pointwise_blocks(h->V), 1, nf);
+    const int slot = prof_begin(h, f64 ? KK_CG_UPDATE_F64 : KK_CG_UPDATE_F32);
+    if (f64)
+        k_cg_update<double><<<g, kThreads, 0, h->stream>>>(u);
+    else
+        k_cg_update<float><<<g, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    return FFTG_OK;
+}
+
+// Runs CG iterations until every one of the nf solves is done. Iterations
+// are enqueued in chunks; kernels of a finished solve return at entry, so a
+// chunk may overrun the last iteration without effect.
+static int run_cg(fftg_handle* h, int nf) {
+    CK(cudaMemcpyAsync(h->h_cg, h->cg, 6 * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int chunk = 2;
+    int launched = 0;
+    const int cap = (h->opt.fixed_cg > 0 ? h->opt.fixed_cg : h->opt.max_cg) + 1;
+    for (;;) {
+        bool all = true;
+        for (int f = 0; f < nf; ++f) all = all && h->h_cg[f].done != CG_RUNNING;
+        if (all) break;
+        if (launched > cap) return FFTG_ENOCONV_CG;  // defensive: should not happen
+        for (int k = 0; k < chunk; ++k) {
+            int rc = launch_cg_iteration(h, nf);
+            if (rc) return rc;
+        }
+        launched += chunk;
+        chunk = std::min(chunk * 2, 16);
+        CK(cudaMemcpyAsync(h->h_cg, h->cg, 6 * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return FFTG_OK;
+}
+
+static void set_cg_params(fftg_handle* h, int nf, double tol) {
+    for (int f = 0; f < 6; ++f) {
+        CGState& c = h->h_cg[f];
+        std::memset(&c, 0, sizeof(CGState));
+        c.tol2 = tol * tol;
+        c.max_it = h->opt.max_cg;
+        c.fixed_it = h->opt.fixed_cg;
+        c.done = f < nf ? CG_RUNNING : CG_CONVERGED;
+    }
+}
+
+// ---------------------------------------------------------------- public API
+extern "C" {
+
+void fftg_default_options(fftg_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FFTG_MIXED;
+    o->max_newton = 50;
+    o->max_cg = 2000;
+    o->cg_inner_floor = 1e-6;
+    o->nrhs_tangent = 6;
+}
+
+const char* fftg_version(void) { return "fftg 0.1 (sm_103a)"; }
+
+int fftg_workspace_size(int N, const fftg_options* opt, size_t* bytes) {
+    if (!bytes || !valid_grid(N)) return FFTG_EINVAL;
+    fftg_options o;
+    if (opt) o = *opt; else fftg_default_options(&o);
+    if (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) return FFTG_EINVAL;
+    *bytes = make_layout(N, o.precision == FFTG_MIXED, o.nrhs_tangent).total;
+    return FFTG_OK;
+}
+
+int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, const fftg_phase* mats,
+                const fftg_options* opt) {
+    if (!out || !phase || !mats || nphase < 1 || nphase > 256 || !valid_grid(N)) return FFTG_EINVAL;
+    *out = nullptr;
+    fftg_options o;
+    if (opt) o = *opt; else fftg_default_options(&o);
+    if ((o.precision != FFTG_FP64 && o.precision != FFTG_MIXED) || o.max_newton < 1 || o.max_cg < 1 ||
+        (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) || o.fixed_cg < 0 || o.fixed_newton < 0)
+        return FFTG_EINVAL;
+    for (int i = 0; i < nphase; ++i)
+        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0))
+            return FFTG_EINVAL;
+    const size_t V = (size_t)N * N * N;
+    for (size_t v = 0; v < V; ++v)
+        if (phase[v] >= nphase) return FFTG_EINVAL;
+
+    fftg_handle* h = new (std::nothrow) fftg_handle();
+    if (!h) return FFTG_ENOMEM;
+    h->N = N;
+    h->V = (long long)V;
+    h->H = (N + 1) / 2;
+    h->mixed = o.precision == FFTG_MIXED;
+    h->nrhs = o.nrhs_tangent;
+    h->opt = o;
+    h->stream = (cudaStream_t)o.stream;
+    h->nphase = nphase;
+    const Layout L = make_layout(N, h->mixed, h->nrhs);
+    if (o.workspace) {
+        if (o.workspace_bytes < L.total || ((uintptr_t)o.workspace & 255u)) {
+            delete h;
+            return FFTG_ENOMEM;
+        }
+        h->ws = (char*)o.workspace;
+        h->own_ws = false;
+    } else {
+        if (cudaMalloc((void**)&h->ws, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return FFTG_ENOMEM;
+        }
+        h->own_ws = true;
+    }
+    h->ws_bytes = L.total;
+    h->phase = (uint8_t*)(h->ws + L.off_phase);
+    h->mats = (double*)(h->ws + L.off_mats);
+    h->eps_star = (double*)(h->ws + L.off_eps_star);
+    h->eps_work = (double*)(h->ws + L.off_eps_work);
+    h->eps_p[0] = (double*)(h->ws + L.off_eps_p0);
+    h->eps_p[1] = (double*)(h->ws + L.off_eps_p1);
+    h->epbar[0] = (double*)(h->ws + L.off_epbar0);
+    h->epbar[1] = (double*)(h->ws + L.off_epbar1);
+    h->sigma = (double*)(h->ws + L.off_sigma);
+    h->tangent = h->ws + L.off_tangent;
+    h->x = h->ws + L.off_x;
+    h->r = h->ws + L.off_r;
+    h->p = h->ws + L.off_p;
+    h->q = h->ws + L.off_q;
+    h->spec = h->ws + L.off_spec;
+    h->tw32 = h->ws + L.off_tw32;
+    h->tw64 = h->ws + L.off_tw64;
+    h->partials = (double*)(h->ws + L.off_partials);
+    h->cg = (CGState*)(h->ws + L.off_cg);
+    h->nd = (NewtonDev*)(h->ws + L.off_nd);
+    h->out36 = (double*)(h->ws + L.off_out36);
+
+    auto fail = [&](int code) {
+        fftg_destroy(h);
+        return code;
+    };
+    if (cudaMallocHost((void**)&h->h_cg, 6 * sizeof(CGState)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_nd, sizeof(NewtonDev)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_out36, 36 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FFTG_ENOMEM);
+    }
+    std::vector<double> tw64(2 * N);
+    std::vector<float> tw32(2 * N);
+    twiddles(N, tw64.data(), tw32.data());
+    std::vector<double> m(4 * nphase);
+    for (int i = 0; i < nphase; ++i) {
+        m[4 * i] = mats[i].K;
+        m[4 * i + 1] = mats[i].G;
+        m[4 * i + 2] = mats[i].sigma_y;
+        m[4 * i + 3] = mats[i].H;
+    }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->phase, phase, V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->mats, m.data(), m.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->tw64, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->tw32, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(h->eps_star, 0, 6 * V * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->eps_p[0], 0, 6 * V * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->epbar[0], 0, V * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->cg, 0, 6 * sizeof(CGState), s) != cudaSuccess ||
+        cudaMemsetAsync(h->nd, 0, sizeof(NewtonDev), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        h->last_cuda = cudaGetLastError();
+        return fail(FFTG_ECUDA);
+    }
+    h->hist = 0;
+    *out = h;
+    return FFTG_OK;
+}
+
+void fftg_destroy(fftg_handle* h) {
+    if (!h) return;
+    if (h->stream || h->ws) cudaStreamSynchronize(h->stream);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->h_cg) cudaFreeHost(h->h_cg);
+    if (h->h_nd) cudaFreeHost(h->h_nd);
+    if (h->h_out36) cudaFreeHost(h->h_out36);
+    if (h->prof) {
+        for (int i = 0; i < Prof::kRing; ++i) {
+            if (h->prof->ev0[i]) cudaEventDestroy(h->prof->ev0[i]);
+            if (h->prof->ev1[i]) cudaEventDestroy(h->prof->ev1[i]);
+        }
+        delete h->prof;
+    }
+    delete h;
+}
+
+int fftg_profile_kinds(void) { return KK_COUNT; }
+
+const char* fftg_profile_name(int kind) {
+    return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : nullptr;
+}
+
+int fftg_profile_enable(fftg_handle* h, int on) {
+    if (!h) return FFTG_EINVAL;
+    if (on && !h->prof) {
+        h->prof = new (std::nothrow) Prof();
+        if (!h->prof) return FFTG_ENOMEM;
+        for (int i = 0; i < Prof::kRing; ++i) {
+            CK(cudaEventCreate(&h->prof->ev0[i]));
+            CK(cudaEventCreate(&h->prof->ev1[i]));
+        }
+    }
+    if (h->prof) {
+        CK(prof_drain(h));
+        h->prof->on = on != 0;
+    }
+    return FFTG_OK;
+}
+
+int fftg_profile_reset(fftg_handle* h) {
+    if (!h) return FFTG_EINVAL;
+    if (h->prof) {
+        CK(prof_drain(h));
+        for (int k = 0; k < KK_COUNT; ++k) {
+            h->prof->ms[k] = 0.0;
+            h->prof->cnt[k] = 0;
+        }
+    }
+    return FFTG_OK;
+}
+
+int fftg_profile_read(fftg_handle* h, int kind, double* total_ms, long long* launches) {
+    if (!h || kind < 0 || kind >= KK_COUNT) return FFTG_EINVAL;
+    if (h->prof) CK(prof_drain(h));
+    if (total_ms) *total_ms = h->prof ? h->prof->ms[kind] : 0.0;
+    if (launches) *launches = h->prof ? h->prof->cnt[kind] : 0;
+    return FFTG_OK;
+}
+
+long long fftg_launch_count(const fftg_handle* h) { return h ? h->launches : 0; }
+
+int fftg_step(fftg_handle* h, const double dE[6], double tol_newton, double tol_cg, double sigma_out[6],
+              int* newton_iters, int* cg_iters) {
+    if (!h || !dE || !sigma_out || !(tol_newton > 0) || !(tol_cg > 0)) return FFTG_EINVAL;
+    for (int c = 0; c < 6; ++c)
+        if (!std::isfinite(dE[c])) return FFTG_ENAN;
+    fftg_stats& st = h->stats;
+    std::memset(&st, 0, sizeof(st));
+    double Et[6];
+    for (int c = 0; c < 6; ++c) Et[c] = h->E[c] + dE[c];
+    const double normE = std::sqrt((double)h->V) * frob6(Et);
+    const double tol_inner = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
+    CK(cudaMemcpyAsync(h->eps_work, h->eps_star, 6 * h->V * 8, cudaMemcpyDeviceToDevice, h->stream));
+    h->have_tangent = false;
+    int it = 0;
+    bool converged = false;
+    int status = FFTG_OK;
+    for (;;) {
+        set_cg_params(h, 1, tol_inner);
+        CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+        int rc = launch_constitutive(h, Et, h->eps_work, h->sigma, false, h->cg);
+        if (rc) return rc;
+        rc = launch_residual(h);
+        if (rc) return rc;
+        rc = run_cg(h, 1);
+        if (rc) return rc;
+        VecArgs u{};
+        u.V = h->V;
+        u.x = h->x;
+        u.eps = h->eps_work;
+        u.nd = h->nd;
+        u.partials = h->partials;
+        const int slot = prof_begin(h, h->mixed ? KK_NEWTON_UPDATE_F32 : KK_NEWTON_UPDATE_F64);
+        if (h->mixed)
+            k_newton_update<float><<<pointwise_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        else
+            k_newton_update<double><<<pointwise_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        prof_end(h, slot);
+        CK(cudaGetLastError());
+        rc = sync_read(h, true, true);
+        if (rc) return rc;
+        const CGState& c = h->h_cg[0];
+        const double nde = std::sqrt(h->h_nd->de2);
+        const double rel = normE > 0 ? nde / normE : (nde == 0 ? 0.0 : INFINITY);
+        if (it < FFTG_MAX_NEWTON_LOG) {
+            st.cg_per_newton[it] = c.it;
+            st.newton_norm[it] = rel;
+            st.residual[it] = h->h_nd->sig2 > 0 ? std::sqrt(c.gs2 / h->h_nd->sig2) : 0.0;
+            st.cg_relres[it] = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
+        }
+        st.cg_iters += c.it;
+        ++it;
+        if (c.done == CG_BREAKDOWN || !std::isfinite(rel)) {
+            status = FFTG_ENAN;
+            break;
+        }
+        if (h->opt.fixed_newton > 0) {
+            if (it >= h->opt.fixed_newton) {
+                converged = true;
+                break;
+            }
+            continue;
+        }
+        if (rel <= tol_newton || nde == 0.0) {
+            converged = true;
+            break;
+        }
+        if (it >= h->opt.max_newton) {
+            status = FFTG_ENOCONV_NEWTON;
+            break;
+        }
+    }
+    st.newton_iters = it;
+    if (newton_iters) *newton_iters = it;
+    if (cg_iters) *cg_iters = st.cg_iters;
+    if (!converged) {
+        st.status = status;
+        return status;
+    }
+    int rc = launch_constitutive(h, Et, h->eps_work, h->sigma, true, nullptr);
+    if (rc) return rc;
+    rc = sync_read(h, false, true);
+    if (rc) return rc;
+    for (int c = 0; c < 6; ++c) sigma_out[c] = h->h_nd->sum[c] / (double)h->V;
+    // commit: the working strain and the updated history become the state
+    std::swap(h->eps_star, h->eps_work);
+    h->hist = 1 - h->hist;
+    for (int c = 0; c < 6; ++c) h->E[c] = Et[c];
+    h->have_tangent = true;
+    st.status = FFTG_OK;
+    return FFTG_OK;
+}
+
+int fftg_last_stats(fftg_handle* h, fftg_stats* out) {
+    if (!h || !out) return FFTG_EINVAL;
+    *out = h->stats;
+    return FFTG_OK;
+}
+
+int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters) {
+    if (!h || !C_out || !(tol_cg > 0)) return FFTG_EINVAL;
+    if (h->nrhs != 6) return FFTG_EINVAL;
+    if (!h->have_tangent) return FFTG_ESTATE;
+    const bool f64 = !h->mixed;
+    const double tol = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
+    set_cg_params(h, 6, tol);
+    CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+    VecArgs u{};
+    u.V = h->V;
+    u.tangent = h->tangent;
+    u.cg = h->cg;
+    u.nd = h->nd;
+    u.partials = h->partials;
+    u.fstride = 6 * h->V;
+    const int nb = pointwise_blocks(h->V);
+    int slot = prof_begin(h, KK_TANGENT_FLOOR);
+    if (f64)
+        k_tangent_floor<double><<<nb, kThreads, 0, h->stream>>>(u);
+    else
+        k_tangent_floor<float><<<nb, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    PassArgs a = base_args(h, f64);
+    a.tangent = h->tangent;
+    a.out = h->spec;
+    CK(pass(h, f64 ? PK_P1_TANRHS_F64 : PK_P1_TANRHS_F32, a, 6));
+    int rc = run_p234(h, f64, -invN3, nullptr, 6);
+    if (rc) return rc;
+    PassArgs b = base_args(h, f64);
+    b.in = h->spec;
+    b.out = h->r;
+    b.cg = h->cg;
+    CK(pass(h, f64 ? PK_P5_RHS_F64_TO_F64 : PK_P5_RHS_F32_TO_F32, b, 6));
+    CK(cudaMemsetAsync(h->x, 0, 6 * 6 * h->V * (h->mixed ? 4 : 8), h->stream));
+    rc = run_cg(h, 6);
+    if (rc) return rc;
+    int total = 0;
+    for (int f = 0; f < 6; ++f) {
+        if (h->h_cg[f].done == CG_BREAKDOWN) return FFTG_ENAN;
+        total += h->h_cg[f].it;
+    }
+    u.x = h->x;
+    u.out = h->out36;
+    slot = prof_begin(h, KK_TANGENT_AVERAGE);
+    if (f64)
+        k_tangent_average<double><<<nb, kThreads, 0, h->stream>>>(u);
+    else
+        k_tangent_average<float><<<nb, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_out36, h->out36, 36 * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 36; ++k) C_out[k] = h->h_out36[k] / (double)h->V;
+    if (cg_iters) *cg_iters = total;
+    return FFTG_OK;
+}
+
+size_t fftg_state_bytes(const fftg_handle* h) {
+    if (!h) return 0;
+    return (size_t)(6 + 13 * h->V) * sizeof(double);
+}
+
+int fftg_get_state(fftg_handle* h, void* buf, size_t bytes) {
+    if (!h || !buf || bytes < fftg_state_bytes(h)) return FFTG_EINVAL;
+    double* d = (double*)buf;
+    std::memcpy(d, h->E, 6 * sizeof(double));
+    CK(cudaMemcpyAsync(d + 6, h->eps_star, 6 * h->V * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(d + 6 + 6 * h->V, h->eps_p[h->hist], 6 * h->V * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(d + 6 + 12 * h->V, h->epbar[h->hist], h->V * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FFTG_OK;
+}
+
+int fftg_set_state(fftg_handle* h, const void* buf, size_t bytes) {
+    if (!h || !buf || bytes < fftg_state_bytes(h)) return FFTG_EINVAL;
+    const double* d = (const double*)buf;
+    for (int c = 0; c < 6; ++c)
+        if (!std::isfinite(d[c])) return FFTG_EINVAL;
+    CK(cudaMemcpyAsync(h->eps_star, d + 6, 6 * h->V * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->eps_p[h->hist], d + 6 + 6 * h->V, 6 * h->V * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->epbar[h->hist], d + 6 + 12 * h->V, h->V * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(h->E, d, 6 * sizeof(double));
+    h->have_tangent = false;
+    return FFTG_OK;
+}
+
+int fftg_get_field(fftg_handle* h, int which, double* out) {
+    if (!h || !out) return FFTG_EINVAL;
+    const size_t V = (size_t)h->V;
+    switch (which) {
+        case FFTG_FIELD_STRAIN: {
+            CK(cudaMemcpyAsync(out, h->eps_star, 6 * V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (int c = 0; c < 6; ++c)
+                for (size_t v = 0; v < V; ++v) out[c * V + v] += h->E[c];
+            return FFTG_OK;
+        }
+        case FFTG_FIELD_STRESS: {
+            // The committed plastic strain is the return-mapped one at the
+            // committed strain, so the trial stress against it is the
+            // converged stress (Phi = 0: elastic branch). The tangent of the
+            // increment is left untouched.
+            int rc = launch_constitutive(h, h->E, h->eps_star, h->sigma, false, nullptr, false);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(out, h->sigma, 6 * V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            return FFTG_OK;
+        }
+        case FFTG_FIELD_EPBAR:
+            CK(cudaMemcpyAsync(out, h->epbar[h->hist], V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            return FFTG_OK;
+        case FFTG_FIELD_EPS_P:
+            CK(cudaMemcpyAsync(out, h->eps_p[h->hist], 6 * V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            return FFTG_OK;
+        default:
+            return FFTG_EINVAL;
+    }
+}
+
+int fftg_op_project(fftg_handle* h, int precision, const void* tau, void* out) {
+    if (!h || !tau || !out || (precision != FFTG_FP64 && precision != FFTG_MIXED)) return FFTG_EINVAL;
+    const bool f64 = precision == FFTG_FP64;
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    PassArgs a = base_args(h, f64);
+    a.in = tau;
+    a.out = h->spec;
+    CK(pass(h, f64 ? PK_P1_PLAIN_F64 : PK_P1_PLAIN_F32, a, 1));
+    int rc = run_p234(h, f64, invN3, nullptr, 1);
+    if (rc) return rc;
+    PassArgs b = base_args(h, f64);
+    b.in = h->spec;
+    b.out = out;
+    CK(pass(h, f64 ? PK_P5_PLAIN_F64 : PK_P5_PLAIN_F32, b, 1));
+    return FFTG_OK;
+}
+
+int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps, double* sigma) {
+    if (!h) return FFTG_EINVAL;
+    double Et[6];
+    for (int c = 0; c < 6; ++c) Et[c] = h->E[c] + (dE ? dE[c] : 0.0);
+    int rc = launch_constitutive(h, Et, eps ? eps : h->eps_star, sigma ? sigma : h->sigma, false, nullptr);
+    if (rc) return rc;
+    h->have_tangent = false;
+    return FFTG_OK;
+}
+
+int fftg_op_matvec(fftg_handle* h, int precision, const void* p, void* q, double* pq) {
+    if (!h || !p || !q) return FFTG_EINVAL;
+    const bool f64 = precision == FFTG_FP64;
+    if (f64 == (bool)h->mixed) return FFTG_EINVAL;  // must match the tangent's precision
+    set_cg_params(h, 1, 1.0);
+    h->h_cg[0].rr = 1.0;
+    CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    PassArgs a = base_args(h, f64);
+    a.in = p;
+    a.tangent = h->tangent;
+    a.out = h->spec;
+    CK(pass(h, f64 ? PK_P1_TAN_F64 : PK_P1_TAN_F32, a, 1));
+    int rc = run_p234(h, f64, invN3, nullptr, 1);
+    if (rc) return rc;
+    PassArgs b = base_args(h, f64);
+    b.in = h->spec;
+    b.out = q;
+    b.aux = p;
+    b.cg = h->cg;
+    CK(pass(h, f64 ? PK_P5_DOT_F64 : PK_P5_DOT_F32, b, 1));
+    if (pq) {
+        CK(cudaMemcpyAsync(h->h_cg, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        *pq = h->h_cg[0].pq;
+    }
+    return FFTG_OK;
+}
+
+}  // extern "C"

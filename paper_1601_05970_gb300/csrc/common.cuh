@@ -1,0 +1,116 @@
+// Device-side state and deterministic reductions shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftg {
+
+constexpr int kThreads = 256;
+
+// Roundoff floor (relative to the norm of the projected field) below which a
+// CG residual is treated as FFT roundoff; see the CG readings.
+constexpr double kRoundoffRel = 1e-13;
+
+// CG status values in CGState::done
+enum : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
+
+// State of one CG solve (one right-hand side), resident on the device so
+// that the iteration needs no host round trip. The last block of each
+// reducing kernel updates it.
+struct CGState {
+    double rr;       // <r, r> of the current residual
+    double rr0;      // <r0, r0>
+    double gs2;      // ||G sigma||^2 of the right-hand side before rounding
+    double tol2;     // relative tolerance squared (set by the host)
+    double floor2;   // absolute roundoff floor squared
+    double stop2;    // max(tol2 * rr0, floor2)
+    double pq;       // <p, q>
+    double alpha;
+    double beta;
+    int it;          // iterations done
+    int max_it;      // cap (set by the host)
+    int fixed_it;    // > 0: exactly this many iterations (set by the host)
+    int done;        // CG_* status
+    unsigned int ticket;  // last-block counter (always 0 between kernels)
+    int pad;
+};
+
+// Scalars of one Newton iteration / one constitutive evaluation.
+struct NewtonDev {
+    double sig2;      // ||sigma||^2 (Frobenius, summed over voxels)
+    double sum[6];    // sum of sigma over voxels, per component
+    double de2;       // ||d eps||^2 of the last Newton update
+    double extra[8];  // reductions of auxiliary kernels (tangent averages)
+    unsigned int ticket;
+    int nplastic;     // unused slot kept for alignment
+};
+
+// Frobenius product of symmetric tensors stored as 6 components
+template <typename T>
+__device__ __forceinline__ T frob(const T* a, const T* b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + T(2) * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a block of kThreads threads (1D); result valid in every thread.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[kThreads / 32];
+    __shared__ double total;
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double s = (lane < kThreads / 32) ? red[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) total = s;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Store this block's NV partial sums and report whether this block is the
+// last one of `nblocks` to do so. Partials of the other blocks are then
+// visible to it (fence before the ticket).
+template <int NV>
+__device__ __forceinline__ bool publish_partials(const double (&v)[NV], double* partials, int bid,
+                                                 int nblocks, unsigned int* ticket) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[(size_t)bid * NV + j] = v[j];
+        __threadfence();
+        unsigned int prev = atomicAdd(ticket, 1u);
+        last = (prev == (unsigned int)(nblocks - 1));
+    }
+    __syncthreads();
+    return last;
+}
+
+// In the last block: totals over all blocks in a fixed order (thread i takes
+// blocks i, i + kThreads, ...; then a fixed tree), so the result does not
+// depend on which block finished last. Resets the ticket.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* partials, int nblocks, unsigned int* ticket,
+                                                double (&tot)[NV]) {
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] += __ldcg(partials + (size_t)b * NV + j);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = block_sum(acc[j]);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+}  // namespace fftg

@@ -1,0 +1,244 @@
+// Odd-radix (3, 5) FFT building blocks for sm_103a.
+//
+// A pencil of length N = N1 * N2 is transformed in two register stages with
+// one shared-memory exchange between them (a Stockham-style four-step
+// decomposition; the DFT pair is that of Eq. (DFT_forward_inverse), with the
+// 1/|N| factor applied by the caller):
+//
+//   index n = t + N2*m  (t < N2, m < N1),   frequency k = k1 + N1*k2
+//   stage A : for each t, an N1-point DFT over m, then the twiddle w_N^{t k1}
+//   stage B : for each k1, an N2-point DFT over t
+//
+// Stage A leaves Y_t[k1] at position t + N2*k1; stage B reads the N2 values
+// at positions N2*k1 + t and writes frequency k1 + N1*k2 either in natural
+// order or back in place at position N2*k1 + k2 (the "permuted" order used
+// when the spectrum stays in shared memory). Every stage reads and writes
+// the same set of positions, so each runs in place without a barrier inside.
+// The inverse runs the same stages backwards with conjugate twiddles.
+//
+// Inside a stage the N1- or N2-point DFT runs in registers, itself split
+// recursively into radix-3 and radix-5 butterflies whose twiddles come from
+// the same table w_N^j (read with warp-uniform indices, i.e. broadcast).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftg {
+
+template <typename T>
+struct __align__(2 * sizeof(T)) cplx {
+    T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> mk(T a, T b) { cplx<T> r; r.x = a; r.y = b; return r; }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return mk(s * a.x, s * a.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> conj(cplx<T> a) { return mk(a.x, -a.y); }
+// i * a
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_i(cplx<T> a) { return mk(-a.y, a.x); }
+
+// Multiply by the table twiddle w = exp(-2 pi i j/N) for the forward
+// direction (S = -1) or by its conjugate for the inverse (S = +1).
+template <int S, typename T>
+__device__ __forceinline__ cplx<T> twmul(cplx<T> v, cplx<T> w) {
+    return S < 0 ? cmul(v, w) : cmulc(v, w);
+}
+
+// ---------------------------------------------------------------- butterflies
+// DFT of 3 or 5 points with kernel exp(S * 2 pi i jk / P), in place.
+template <int P, int S, typename T>
+struct Butterfly;
+
+template <int S, typename T>
+struct Butterfly<3, S, T> {
+    static __device__ __forceinline__ void run(cplx<T>* a) {
+        const T h = T(0.86602540378443864676);  // sqrt(3)/2
+        cplx<T> t1 = a[1] + a[2];
+        cplx<T> t2 = a[1] - a[2];
+        cplx<T> m = a[0] - T(0.5) * t1;
+        cplx<T> r = mul_i(t2);
+        r = T(S) * h * r;
+        a[0] = a[0] + t1;
+        a[1] = m + r;
+        a[2] = m - r;
+    }
+};
+
+template <int S, typename T>
+struct Butterfly<5, S, T> {
+    static __device__ __forceinline__ void run(cplx<T>* a) {
+        const T c1 = T(0.30901699437494742410);   // cos(2 pi/5)
+        const T c2 = T(-0.80901699437494742410);  // cos(4 pi/5)
+        const T s1 = T(0.95105651629515357212);   // sin(2 pi/5)
+        const T s2 = T(0.58778525229247312917);   // sin(4 pi/5)
+        cplx<T> b1 = a[1] + a[4], b2 = a[2] + a[3];
+        cplx<T> d1 = a[1] - a[4], d2 = a[2] - a[3];
+        cplx<T> A1 = a[0] + c1 * b1 + c2 * b2;
+        cplx<T> A2 = a[0] + c2 * b1 + c1 * b2;
+        cplx<T> B1 = mul_i(s1 * d1 + s2 * d2);
+        cplx<T> B2 = mul_i(s2 * d1 - s1 * d2);
+        B1 = T(S) * B1;
+        B2 = T(S) * B2;
+        a[0] = a[0] + b1 + b2;
+        a[1] = A1 + B1;
+        a[4] = A1 - B1;
+        a[2] = A2 + B2;
+        a[3] = A2 - B2;
+    }
+};
+
+// ---------------------------------------------------------------- register DFT
+// R-point DFT in registers (R = 3^a 5^b), natural order in and out.
+// Split R = P*Q with P the smallest factor: n = q + Q*p, k = k1 + P*k2.
+template <int N, int R, int S, typename T>
+struct RegDFT {
+    static __device__ __forceinline__ void run(cplx<T> (&a)[R], const cplx<T>* __restrict__ tw) {
+        constexpr int P = (R % 3 == 0) ? 3 : 5;
+        constexpr int Q = R / P;
+        static_assert(P * Q == R, "R must be a product of 3 and 5");
+        cplx<T> y[R];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            cplx<T> v[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) v[p] = a[q + Q * p];
+            Butterfly<P, S, T>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) {
+                if (q * k1 == 0) {
+                    y[k1 * Q + q] = v[k1];
+                } else {
+                    y[k1 * Q + q] = twmul<S>(v[k1], tw[(q * k1 * (N / R)) % N]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            cplx<T> z[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) z[q] = y[k1 * Q + q];
+            RegDFT<N, Q, S, T>::run(z, tw);
+#pragma unroll
+            for (int k2 = 0; k2 < Q; ++k2) a[k1 + P * k2] = z[k2];
+        }
+    }
+};
+
+template <int N, int S, typename T>
+struct RegDFT<N, 1, S, T> {
+    static __device__ __forceinline__ void run(cplx<T> (&)[1], const cplx<T>* __restrict__) {}
+};
+
+// ---------------------------------------------------------------- plans
+// N = N1 * N2: N1 points per thread in stage A, N2 in stage B.
+template <int N>
+struct Plan;
+#define FFTG_PLAN(n, a, b)                          \
+    template <>                                     \
+    struct Plan<n> {                                \
+        static constexpr int N1 = a, N2 = b;        \
+    };
+FFTG_PLAN(3, 3, 1)
+FFTG_PLAN(5, 5, 1)
+FFTG_PLAN(9, 9, 1)
+FFTG_PLAN(15, 15, 1)
+FFTG_PLAN(25, 25, 1)
+FFTG_PLAN(27, 27, 1)
+FFTG_PLAN(45, 9, 5)
+FFTG_PLAN(75, 15, 5)
+FFTG_PLAN(81, 9, 9)
+FFTG_PLAN(125, 25, 5)
+FFTG_PLAN(135, 15, 9)
+FFTG_PLAN(225, 15, 15)
+FFTG_PLAN(243, 27, 9)
+#undef FFTG_PLAN
+
+// position of frequency k after a forward stage B in permuted mode
+template <int N>
+__device__ __forceinline__ int perm_pos(int k) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    return N2 * (k % N1) + k / N1;
+}
+
+// ---------------------------------------------------------------- stages
+// src/dst: pencil base pointers; ss/ds: element strides (in cplx units).
+
+// forward stage A: reads positions t + N2*m, writes t + N2*k1 (with twiddle)
+template <int N, typename T>
+__device__ __forceinline__ void fwdA(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int t,
+                                     const cplx<T>* __restrict__ tw) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    cplx<T> v[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = src[(t + N2 * m) * ss];
+    RegDFT<N, N1, -1, T>::run(v, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        cplx<T> y = v[k1];
+        if (N2 > 1 && k1 > 0) y = twmul<-1>(y, tw[(t * k1) % N]);
+        dst[(t + N2 * k1) * ds] = y;
+    }
+}
+
+// forward stage B: reads N2*k1 + q; NATURAL: writes k1 + N1*k2, else N2*k1 + k2
+template <int N, bool NATURAL, typename T>
+__device__ __forceinline__ void fwdB(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int k1,
+                                     const cplx<T>* __restrict__ tw) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    cplx<T> v[N2];
+#pragma unroll
+    for (int q = 0; q < N2; ++q) v[q] = src[(N2 * k1 + q) * ss];
+    RegDFT<N, N2, -1, T>::run(v, tw);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) dst[(NATURAL ? (k1 + N1 * k2) : (N2 * k1 + k2)) * ds] = v[k2];
+}
+
+// inverse stage B': NATURAL: reads k1 + N1*k2, else N2*k1 + k2;
+// writes N2*k1 + t with the conjugate twiddle
+template <int N, bool NATURAL, typename T>
+__device__ __forceinline__ void invB(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int k1,
+                                     const cplx<T>* __restrict__ tw) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    cplx<T> v[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[(NATURAL ? (k1 + N1 * k2) : (N2 * k1 + k2)) * ss];
+    RegDFT<N, N2, +1, T>::run(v, tw);
+#pragma unroll
+    for (int t = 0; t < N2; ++t) {
+        cplx<T> z = v[t];
+        if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[(t * k1) % N]);
+        dst[(N2 * k1 + t) * ds] = z;
+    }
+}
+
+// inverse stage A': reads t + N2*k1, writes t + N2*m
+template <int N, typename T>
+__device__ __forceinline__ void invA(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int t,
+                                     const cplx<T>* __restrict__ tw) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    cplx<T> v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(t + N2 * k1) * ss];
+    RegDFT<N, N1, +1, T>::run(v, tw);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) dst[(t + N2 * m) * ds] = v[m];
+}
+
+}  // namespace fftg

@@ -1,0 +1,295 @@
+// Pointwise kernels of the Newton-CG path: the J2 return mapping with its
+// consistent tangent (Section 4.2), the CG vector updates (Hestenes-Stiefel)
+// with their reductions, the Newton update eps* += d eps (Algorithm 1), and
+// the reductions of the macroscopic tangent.
+#pragma once
+
+#include "common.cuh"
+
+namespace fftg {
+
+// Maximum grid of the grid-stride pointwise kernels (fixed per V, so the
+// reduction order never depends on timing).
+constexpr int kMaxPointwiseBlocks = 4096;
+
+inline int pointwise_blocks(long long V) {
+    long long b = (V + kThreads - 1) / kThreads;
+    return (int)(b < kMaxPointwiseBlocks ? b : kMaxPointwiseBlocks);
+}
+
+struct ConstArgs {
+    long long V;
+    double E[6];
+    const double* eps;       // [6][V] fluctuation eps*
+    const double* eps_p;     // [6][V] committed plastic strain
+    const double* epbar;     // [V] committed accumulated plastic strain
+    const uint8_t* phase;    // [V]
+    const double* mats;      // [nphase][4] = K, G, sigma_y, H
+    double* sigma;           // [6][V] out (may be null)
+    double* eps_p_new;       // [6][V] out (may be null)
+    double* epbar_new;       // [V] out (may be null)
+    void* tangent;           // [7][V] out in TT (may be null)
+    double* partials;        // [nblocks][7]
+    NewtonDev* nd;           // sig2 and sum of sigma
+    CGState* cg;             // if set: cg->floor2 from ||sigma||
+    double tie;              // plastic iff Phi_trial > tie * sigma_y
+};
+
+// Elastic predictor / plastic corrector with linear hardening (n = 1):
+// trial sigma = C_e : (eps - eps_p^t); Phi = sigma_eq - (sigma_y + H epbar^t);
+// if Phi > tie*sigma_y: dgamma = Phi / (3G + H), N = 3/2 s / sigma_eq,
+// eps_p += dgamma N, epbar += dgamma, sigma -= 2G dgamma N, and the tangent
+// C = C_e - 6G^2 dgamma/sigma_eq I_d + 4G^2 (dgamma/sigma_eq - 1/(3G+H)) N(x)N
+// stored as K, 2G_eff, w = sqrt(-b) N (b the N(x)N coefficient, negative).
+template <typename TT>
+__global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
+    const long long V = a.V;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    TT* tg = (TT*)a.tangent;
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+        const int ph = a.phase[v];
+        const double K = a.mats[4 * ph], G = a.mats[4 * ph + 1], sy = a.mats[4 * ph + 2],
+                     Hh = a.mats[4 * ph + 3];
+        double e[6], ep[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            ep[c] = a.eps_p[c * V + v];
+            e[c] = a.E[c] + a.eps[c * V + v] - ep[c];
+        }
+        const double eb = a.epbar[v];
+        const double tr = e[0] + e[1] + e[2];
+        const double m = tr / 3.0;
+        double s[6];
+        s[0] = 2.0 * G * (e[0] - m);
+        s[1] = 2.0 * G * (e[1] - m);
+        s[2] = 2.0 * G * (e[2] - m);
+        s[3] = 2.0 * G * e[3];
+        s[4] = 2.0 * G * e[4];
+        s[5] = 2.0 * G * e[5];
+        const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
+                          2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+        const double seq = sqrt(1.5 * ss);
+        const double phi = seq - (sy + Hh * eb);
+        double sig[6];
+        double g2 = 2.0 * G;
+        double w[6] = {0, 0, 0, 0, 0, 0};
+        double dg = 0.0;
+        if (phi > a.tie * sy) {
+            dg = phi / (3.0 * G + Hh);
+            const double f = 1.5 / seq;
+            double Nn[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                sig[c] = s[c] - 2.0 * G * dg * Nn[c];
+                ep[c] += dg * Nn[c];
+            }
+            g2 = 2.0 * G - 6.0 * G * G * dg / seq;
+            const double b = 4.0 * G * G * (dg / seq - 1.0 / (3.0 * G + Hh));
+            const double sb = sqrt(fmax(-b, 0.0));
+#pragma unroll
+            for (int c = 0; c < 6; ++c) w[c] = sb * Nn[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sig[c] = s[c];
+        }
+        const double kt = K * tr;
+        sig[0] += kt;
+        sig[1] += kt;
+        sig[2] += kt;
+        if (a.sigma) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) a.sigma[c * V + v] = sig[c];
+        }
+        if (a.eps_p_new) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) a.eps_p_new[c * V + v] = ep[c];
+        }
+        if (a.epbar_new) a.epbar_new[v] = eb + dg;
+        if (tg) {
+            tg[v] = (TT)K;
+            tg[V + v] = (TT)g2;
+            tg[2 * V + v] = (TT)w[0];
+            tg[3 * V + v] = (TT)w[1];
+            tg[4 * V + v] = (TT)w[3];
+            tg[5 * V + v] = (TT)w[4];
+            tg[6 * V + v] = (TT)w[5];
+        }
+        acc[0] += frob<double>(sig, sig);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[1 + c] += sig[c];
+    }
+    double part[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) part[j] = block_sum(acc[j]);
+    if (!publish_partials<7>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
+    double tot[7];
+    reduce_partials<7>(a.partials, gridDim.x, &a.nd->ticket, tot);
+    if (threadIdx.x == 0) {
+        a.nd->sig2 = tot[0];
+        for (int c = 0; c < 6; ++c) a.nd->sum[c] = tot[1 + c];
+        if (a.cg) a.cg->floor2 = kRoundoffRel * kRoundoffRel * tot[0];
+    }
+}
+
+struct VecArgs {
+    long long V;
+    void* x;
+    void* r;
+    const void* p;
+    const void* q;
+    double* eps;       // newton update: eps* (FP64)
+    CGState* cg;
+    NewtonDev* nd;
+    double* partials;  // [nf][nblocks][NV]
+    long long fstride;
+    const void* tangent;
+    double* out;       // tangent averages
+};
+
+// x += alpha p; r -= alpha q; rr = <r, r>; then beta, stopping test.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
+    const int f = blockIdx.z;
+    CGState* cg = a.cg + f;
+    if (cg->done) return;
+    const long long V = a.V;
+    const T alpha = (T)cg->alpha;
+    T* x = (T*)a.x + f * a.fstride;
+    T* r = (T*)a.r + f * a.fstride;
+    const T* p = (const T*)a.p + f * a.fstride;
+    const T* q = (const T*)a.q + f * a.fstride;
+    T acc = T(0);
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+        T rv[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            x[c * V + v] += alpha * p[c * V + v];
+            rv[c] = r[c * V + v] - alpha * q[c * V + v];
+            r[c * V + v] = rv[c];
+        }
+        acc += frob<T>(rv, rv);
+    }
+    double part[1] = {block_sum((double)acc)};
+    double* partials = a.partials + (size_t)f * gridDim.x;
+    if (!publish_partials<1>(part, partials, blockIdx.x, gridDim.x, &cg->ticket)) return;
+    double tot[1];
+    reduce_partials<1>(partials, gridDim.x, &cg->ticket, tot);
+    if (threadIdx.x != 0) return;
+    const double rr = tot[0];
+    const int it = cg->it + 1;
+    cg->it = it;
+    cg->beta = rr / cg->rr;
+    cg->rr = rr;
+    if (!isfinite(rr)) {
+        cg->done = CG_BREAKDOWN;
+    } else if (cg->fixed_it > 0) {
+        if (it >= cg->fixed_it) cg->done = CG_CONVERGED;
+    } else if (rr <= cg->stop2) {
+        cg->done = CG_CONVERGED;
+    } else if (it >= cg->max_it) {
+        cg->done = CG_MAXIT;
+    }
+}
+
+// eps* += x (Algorithm 1, iterative update); nd->de2 = ||x||^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
+    const long long V = a.V;
+    const T* x = (const T*)a.x;
+    double acc = 0.0;
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+        double d[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            d[c] = (double)x[c * V + v];
+            a.eps[c * V + v] += d[c];
+        }
+        acc += frob<double>(d, d);
+    }
+    double part[1] = {block_sum(acc)};
+    if (!publish_partials<1>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
+    double tot[1];
+    reduce_partials<1>(a.partials, gridDim.x, &a.nd->ticket, tot);
+    if (threadIdx.x == 0) a.nd->de2 = tot[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void tangent_apply_v(const T* __restrict__ tg, long long v, long long V,
+                                                const double (&p)[6], double (&s)[6]) {
+    const double K = tg[v], g2 = tg[V + v];
+    const double w0 = tg[2 * V + v], w1 = tg[3 * V + v], w3 = tg[4 * V + v], w4 = tg[5 * V + v],
+                 w5 = tg[6 * V + v];
+    const double w2 = -(w0 + w1);
+    const double tr = p[0] + p[1] + p[2], m = tr / 3.0;
+    const double wp = w0 * p[0] + w1 * p[1] + w2 * p[2] + 2.0 * (w3 * p[3] + w4 * p[4] + w5 * p[5]);
+    s[0] = K * tr + g2 * (p[0] - m) - wp * w0;
+    s[1] = K * tr + g2 * (p[1] - m) - wp * w1;
+    s[2] = K * tr + g2 * (p[2] - m) - wp * w2;
+    s[3] = g2 * p[3] - wp * w3;
+    s[4] = g2 * p[4] - wp * w4;
+    s[5] = g2 * p[5] - wp * w5;
+}
+
+// Roundoff floors of the six tangent right-hand sides: ||C : E_j||^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_tangent_floor(VecArgs a) {
+    const long long V = a.V;
+    const T* tg = (const T*)a.tangent;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            double e[6] = {0, 0, 0, 0, 0, 0}, s[6];
+            e[j] = 1.0;
+            tangent_apply_v<T>(tg, v, V, e, s);
+            acc[j] += frob<double>(s, s);
+        }
+    }
+    double part[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) part[j] = block_sum(acc[j]);
+    if (!publish_partials<6>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
+    double tot[6];
+    reduce_partials<6>(a.partials, gridDim.x, &a.nd->ticket, tot);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 6; ++j) a.cg[j].floor2 = kRoundoffRel * kRoundoffRel * tot[j];
+}
+
+// out[i*6 + j] = sum over voxels of (C : (E_j + x_j))_i
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_tangent_average(VecArgs a) {
+    const long long V = a.V;
+    const T* tg = (const T*)a.tangent;
+    const T* x = (const T*)a.x;
+    double acc[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            double e[6], s[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) e[c] = (double)x[j * a.fstride + c * V + v] + (c == j ? 1.0 : 0.0);
+            tangent_apply_v<T>(tg, v, V, e, s);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) acc[i * 6 + j] += s[i];
+        }
+    }
+    double part[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) part[k] = block_sum(acc[k]);
+    if (!publish_partials<36>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
+    double tot[36];
+    reduce_partials<36>(a.partials, gridDim.x, &a.nd->ticket, tot);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 36; ++k) a.out[k] = tot[k];
+}
+
+}  // namespace fftg

@@ -1,0 +1,282 @@
+"""Thin Python binding of the fftg C-ABI (include/fftg.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+kernels of libfftg.so. The functions keep the C names; `Cell` wraps a
+handle with PyTorch-allocated device memory and the current torch stream.
+There is no CPU fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfftg.so")
+
+FFTG_OK = 0
+FFTG_EINVAL = -1
+FFTG_ENOMEM = -2
+FFTG_ENOCONV_NEWTON = -3
+FFTG_ENOCONV_CG = -4
+FFTG_ENAN = -5
+FFTG_ECUDA = -6
+FFTG_ESTATE = -7
+FFTG_FP64 = 0
+FFTG_MIXED = 1
+FFTG_FIELD_STRAIN = 0
+FFTG_FIELD_STRESS = 1
+FFTG_FIELD_EPBAR = 2
+FFTG_FIELD_EPS_P = 3
+FFTG_MAX_NEWTON_LOG = 64
+
+ERRORS = {
+    FFTG_EINVAL: "invalid argument",
+    FFTG_ENOMEM: "out of device memory / workspace too small",
+    FFTG_ENOCONV_NEWTON: "Newton did not converge",
+    FFTG_ENOCONV_CG: "CG did not converge",
+    FFTG_ENAN: "NaN or Inf in a residual",
+    FFTG_ECUDA: "CUDA error",
+    FFTG_ESTATE: "call out of order",
+}
+
+
+class FftgError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {ERRORS.get(code, 'error')} ({code})")
+        self.code = code
+
+
+class fftg_phase(C.Structure):
+    _fields_ = [("K", C.c_double), ("G", C.c_double), ("sigma_y", C.c_double), ("H", C.c_double)]
+
+
+class fftg_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_newton", C.c_int), ("max_cg", C.c_int),
+                ("cg_inner_floor", C.c_double), ("fixed_cg", C.c_int), ("fixed_newton", C.c_int),
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+                ("nrhs_tangent", C.c_int)]
+
+
+class fftg_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("cg_iters", C.c_int),
+                ("cg_per_newton", C.c_int * FFTG_MAX_NEWTON_LOG),
+                ("newton_norm", C.c_double * FFTG_MAX_NEWTON_LOG),
+                ("residual", C.c_double * FFTG_MAX_NEWTON_LOG),
+                ("cg_relres", C.c_double * FFTG_MAX_NEWTON_LOG)]
+
+
+# every symbol include/fftg.h declares, with its ctypes signature
+_D6 = C.POINTER(C.c_double)
+SIGNATURES = {
+    "fftg_default_options": (None, [C.POINTER(fftg_options)]),
+    "fftg_version": (C.c_char_p, []),
+    "fftg_workspace_size": (C.c_int, [C.c_int, C.POINTER(fftg_options), C.POINTER(C.c_size_t)]),
+    "fftg_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint8), C.c_int,
+                              C.POINTER(fftg_phase), C.POINTER(fftg_options)]),
+    "fftg_step": (C.c_int, [C.c_void_p, _D6, C.c_double, C.c_double, _D6,
+                            C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fftg_last_stats": (C.c_int, [C.c_void_p, C.POINTER(fftg_stats)]),
+    "fftg_tangent": (C.c_int, [C.c_void_p, C.c_double, _D6, C.POINTER(C.c_int)]),
+    "fftg_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "fftg_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fftg_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fftg_get_field": (C.c_int, [C.c_void_p, C.c_int, _D6]),
+    "fftg_destroy": (None, [C.c_void_p]),
+    "fftg_op_project": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "fftg_op_constitutive": (C.c_int, [C.c_void_p, _D6, C.c_void_p, C.c_void_p]),
+    "fftg_op_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, _D6]),
+    "fftg_profile_kinds": (C.c_int, []),
+    "fftg_profile_name": (C.c_char_p, [C.c_int]),
+    "fftg_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "fftg_profile_reset": (C.c_int, [C.c_void_p]),
+    "fftg_profile_read": (C.c_int, [C.c_void_p, C.c_int, _D6, C.POINTER(C.c_longlong)]),
+    "fftg_launch_count": (C.c_longlong, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfftg.so (raises OSError if it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libfftg.so not built at {path}; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(code, where):
+    if code != FFTG_OK:
+        raise FftgError(code, where)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D6)
+
+
+def default_options() -> fftg_options:
+    o = fftg_options()
+    load().fftg_default_options(C.byref(o))
+    return o
+
+
+def workspace_size(N: int, opt: fftg_options) -> int:
+    b = C.c_size_t(0)
+    check(load().fftg_workspace_size(N, C.byref(opt), C.byref(b)), "fftg_workspace_size")
+    return b.value
+
+
+class Cell:
+    """One periodic cell (handle) whose device memory comes from PyTorch.
+
+    phase: uint8 [N, N, N] (x1 slowest); mats: sequence of (K, G, sigma_y, H).
+    """
+
+    def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
+                 cg_inner_floor=1e-6, fixed_cg=0, fixed_newton=0, nrhs_tangent=6,
+                 device=None, stream=None):
+        import torch
+
+        lib = load()
+        self.N = int(N)
+        self.V = self.N ** 3
+        opt = default_options()
+        opt.precision = FFTG_MIXED if precision == "mixed" else FFTG_FP64
+        opt.max_newton = max_newton
+        opt.max_cg = max_cg
+        opt.cg_inner_floor = cg_inner_floor
+        opt.fixed_cg = fixed_cg
+        opt.fixed_newton = fixed_newton
+        opt.nrhs_tangent = nrhs_tangent
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        nbytes = workspace_size(self.N, opt)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        opt.workspace = C.c_void_p((base + 255) & ~255)
+        opt.workspace_bytes = nbytes
+        self.precision = precision
+        ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8).reshape(-1))
+        m = (fftg_phase * len(mats))(*[fftg_phase(*map(float, (t.as_tuple() if hasattr(t, "as_tuple") else t)))
+                                      for t in mats])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib.fftg_create(C.byref(h), self.N, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                  len(mats), m, C.byref(opt)), "fftg_create")
+        self.h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.fftg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- Algorithm 1 --------------------------------------------------------
+    def step(self, dE, tol_newton, tol_cg):
+        dE = np.ascontiguousarray(dE, dtype=np.float64).reshape(6)
+        sig = np.zeros(6)
+        nn, nc = C.c_int(0), C.c_int(0)
+        check(self._lib.fftg_step(self.h, _dptr(dE), tol_newton, tol_cg, _dptr(sig),
+                                  C.byref(nn), C.byref(nc)), "fftg_step")
+        return sig, nn.value, nc.value
+
+    def stats(self):
+        s = fftg_stats()
+        check(self._lib.fftg_last_stats(self.h, C.byref(s)), "fftg_last_stats")
+        n = min(s.newton_iters, FFTG_MAX_NEWTON_LOG)
+        return dict(status=s.status, newton_iters=s.newton_iters, cg_iters=s.cg_iters,
+                    cg_per_newton=list(s.cg_per_newton[:n]),
+                    newton_norm=list(s.newton_norm[:n]), residual=list(s.residual[:n]),
+                    cg_relres=list(s.cg_relres[:n]))
+
+    def tangent(self, tol_cg):
+        out = np.zeros(36)
+        nc = C.c_int(0)
+        check(self._lib.fftg_tangent(self.h, tol_cg, _dptr(out), C.byref(nc)), "fftg_tangent")
+        return out.reshape(6, 6), nc.value
+
+    # -- state --------------------------------------------------------------
+    def get_state(self):
+        n = self._lib.fftg_state_bytes(self.h)
+        buf = np.zeros(n // 8)
+        check(self._lib.fftg_get_state(self.h, buf.ctypes.data_as(C.c_void_p), n), "fftg_get_state")
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.float64)
+        check(self._lib.fftg_set_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes),
+              "fftg_set_state")
+
+    def field(self, which):
+        n = self.V if which == FFTG_FIELD_EPBAR else 6 * self.V
+        out = np.zeros(n)
+        check(self._lib.fftg_get_field(self.h, which, _dptr(out)), "fftg_get_field")
+        return out.reshape((self.N,) * 3 if which == FFTG_FIELD_EPBAR else (6,) + (self.N,) * 3)
+
+    # -- operators on device tensors ---------------------------------------
+    def project(self, tau, out=None):
+        import torch
+        assert tau.is_cuda and tau.is_contiguous() and tau.numel() == 6 * self.V
+        prec = FFTG_FP64 if tau.dtype == torch.float64 else FFTG_MIXED
+        if out is None:
+            out = torch.empty_like(tau)
+        check(self._lib.fftg_op_project(self.h, prec, C.c_void_p(tau.data_ptr()),
+                                        C.c_void_p(out.data_ptr())), "fftg_op_project")
+        return out
+
+    def constitutive(self, dE=None, eps=None, sigma=None):
+        import torch
+        d = None if dE is None else np.ascontiguousarray(dE, dtype=np.float64).reshape(6)
+        if sigma is None:
+            sigma = torch.empty(6 * self.V, dtype=torch.float64, device=self.device)
+        check(self._lib.fftg_op_constitutive(
+            self.h, None if d is None else _dptr(d),
+            None if eps is None else C.c_void_p(eps.data_ptr()),
+            C.c_void_p(sigma.data_ptr())), "fftg_op_constitutive")
+        return sigma
+
+    # -- profiling ------------------------------------------------------------
+    def profile(self, on=True):
+        check(self._lib.fftg_profile_enable(self.h, 1 if on else 0), "fftg_profile_enable")
+
+    def profile_reset(self):
+        check(self._lib.fftg_profile_reset(self.h), "fftg_profile_reset")
+
+    def profile_read(self):
+        """{kernel kind name: (total device ms, launches)} since the last reset."""
+        out = {}
+        for k in range(self._lib.fftg_profile_kinds()):
+            ms, n = C.c_double(0.0), C.c_longlong(0)
+            check(self._lib.fftg_profile_read(self.h, k, C.byref(ms), C.byref(n)), "fftg_profile_read")
+            if n.value:
+                out[self._lib.fftg_profile_name(k).decode()] = (ms.value, n.value)
+        return out
+
+    def launch_count(self):
+        return self._lib.fftg_launch_count(self.h)
+
+    def matvec(self, p, q=None):
+        import torch
+        prec = FFTG_FP64 if p.dtype == torch.float64 else FFTG_MIXED
+        if q is None:
+            q = torch.empty_like(p)
+        pq = C.c_double(0.0)
+        check(self._lib.fftg_op_matvec(self.h, prec, C.c_void_p(p.data_ptr()),
+                                       C.c_void_p(q.data_ptr()), C.byref(pq)), "fftg_op_matvec")
+        return q, pq.value

@@ -172,11 +172,12 @@ def random_increment(seed: int, norm: float = 1e-3) -> np.ndarray:
     return v * (norm / frobenius6(v))
 
 
-def workload(name: str):
+def workload(name: str, seed: int | None = None):
     """Named workloads with their sizes (see the docstrings of the generators).
 
     Returns a dict with keys N, phase (uint8 [N,N,N]), mats (tuple of Phase),
-    dE (increments [n, 6]), tol_newton, tol_cg and a description.
+    dE (increments [n, 6]), tol_newton, tol_cg and a description. `seed`
+    replaces the microstructure seed of the random-sphere workloads.
     """
     if name == "laminate15":
         N = 15
@@ -186,16 +187,18 @@ def workload(name: str):
                          "pure shear to 0.02 in 10 increments")
     if name == "spheres135":
         N = 135
-        ph, frac, _ = random_spheres(N, 0.3, seed=1)
+        seed = 1 if seed is None else seed
+        ph, frac, _ = random_spheres(N, 0.3, seed=seed)
         return dict(N=N, phase=ph, mats=TWO_PHASE, dE=shear_path(0.02, 20),
-                    tol_newton=1e-5, tol_cg=1e-8, fraction=frac,
-                    desc="135^3 random spheres r in [3,8], hard fraction 0.3, "
-                         "seed 1, pure shear to 0.02 in 20 increments")
+                    tol_newton=1e-5, tol_cg=1e-8, fraction=frac, seed=seed,
+                    desc=f"135^3 random spheres r in [3,8], hard fraction 0.3, "
+                         f"seed {seed}, pure shear to 0.02 in 20 increments")
     if name == "spheres243":
         N = 243
-        ph, frac, _ = random_spheres(N, 0.2, seed=2)
+        seed = 2 if seed is None else seed
+        ph, frac, _ = random_spheres(N, 0.2, seed=seed)
         return dict(N=N, phase=ph, mats=TWO_PHASE, dE=uniaxial_path(0.03, 20),
-                    tol_newton=1e-5, tol_cg=1e-8, fraction=frac,
-                    desc="243^3 random spheres r in [3,8], hard fraction 0.2, "
-                         "seed 2, uniaxial strain E11 to 0.03 in 20 increments")
+                    tol_newton=1e-5, tol_cg=1e-8, fraction=frac, seed=seed,
+                    desc=f"243^3 random spheres r in [3,8], hard fraction 0.2, "
+                         f"seed {seed}, uniaxial strain E11 to 0.03 in 20 increments")
     raise KeyError(name)
