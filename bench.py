@@ -228,6 +228,7 @@ def main():
     launches0 = cell.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()  # profiler range = the timed region (no effect without one)
     ev0.record(stream)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -235,6 +236,7 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
+    torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clocks = sampler.stop() if not args.no_clocks else None

@@ -102,6 +102,10 @@ typedef struct {
     double newton_norm[FFTG_MAX_NEWTON_LOG];    /* ||d eps*|| / ||E||_field, Algorithm 1 Newton test */
     double residual[FFTG_MAX_NEWTON_LOG];       /* ||G sigma|| / ||sigma|| (Table 3 analogue) */
     double cg_relres[FFTG_MAX_NEWTON_LOG];      /* final recursive ||r||/||r0|| of each solve */
+    int    cg_status[FFTG_MAX_NEWTON_LOG];      /* how each solve ended: 1 converged, 2 max_cg
+                                                   reached, 4 stagnated (FFTG_MIXED inner solve:
+                                                   no progress for 25 iterations, or a
+                                                   non-positive <p, Ap> from rounding) */
 } fftg_stats;
 
 /* Fill *opt with the defaults listed above. */

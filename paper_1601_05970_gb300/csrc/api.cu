@@ -415,6 +415,10 @@ static int run_cg(fftg_handle* h, int nf) {
     return FFTG_OK;
 }
 
+// Iterations without a new minimum of <r, r> after which an FP32 inner
+// solve is considered stagnated.
+constexpr int kStagWindow = 25;
+
 static void set_cg_params(fftg_handle* h, int nf, double tol) {
     for (int f = 0; f < 6; ++f) {
         CGState& c = h->h_cg[f];
@@ -422,6 +426,8 @@ static void set_cg_params(fftg_handle* h, int nf, double tol) {
         c.tol2 = tol * tol;
         c.max_it = h->opt.max_cg;
         c.fixed_it = h->opt.fixed_cg;
+        // the FP32 inner solve stops when it stagnates (FP64 Newton refines)
+        c.stag_window = (h->mixed && h->opt.fixed_cg <= 0) ? kStagWindow : 0;
         c.done = f < nf ? CG_RUNNING : CG_CONVERGED;
     }
 }
@@ -664,6 +670,7 @@ int fftg_step(fftg_handle* h, const double dE[6], double tol_newton, double tol_
             st.newton_norm[it] = rel;
             st.residual[it] = h->h_nd->sig2 > 0 ? std::sqrt(c.gs2 / h->h_nd->sig2) : 0.0;
             st.cg_relres[it] = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
+            st.cg_status[it] = c.done;
         }
         st.cg_iters += c.it;
         ++it;

@@ -12,8 +12,12 @@ constexpr int kThreads = 256;
 // CG residual is treated as FFT roundoff; see the CG readings.
 constexpr double kRoundoffRel = 1e-13;
 
-// CG status values in CGState::done
-enum : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
+// CG status values in CGState::done. CG_STAGNATED ends an inner (FP32)
+// solve that has stopped improving: no new minimum of <r, r> for
+// `stag_window` iterations, or a finite <p, q> <= 0 (rounding noise has
+// overtaken the search direction). The iterate is kept and the FP64 Newton
+// iteration refines it. CG_BREAKDOWN is a NaN or Inf.
+enum : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_STAGNATED = 4 };
 
 // State of one CG solve (one right-hand side), resident on the device so
 // that the iteration needs no host round trip. The last block of each
@@ -28,6 +32,9 @@ struct CGState {
     double pq;       // <p, q>
     double alpha;
     double beta;
+    double rr_min;   // smallest <r, r> so far
+    int it_min;      // iteration of rr_min
+    int stag_window; // > 0: stagnation test window (set by the host)
     int it;          // iterations done
     int max_it;      // cap (set by the host)
     int fixed_it;    // > 0: exactly this many iterations (set by the host)

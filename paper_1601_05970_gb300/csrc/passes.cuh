@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
     if (MODE == P5_DOT) {
         const double pq = tot[0];
         cg->pq = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) {
+        if (!isfinite(pq)) {
             cg->done = CG_BREAKDOWN;
+        } else if (!(pq > 0.0)) {
+            cg->done = cg->stag_window > 0 ? CG_STAGNATED : CG_BREAKDOWN;
         } else {
             cg->alpha = cg->rr / pq;
         }
@@ -409,6 +411,8 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
         const double rr = tot[0], gs2 = tot[1];
         cg->rr = rr;
         cg->rr0 = rr;
+        cg->rr_min = rr;
+        cg->it_min = 0;
         cg->gs2 = gs2;
         cg->it = 0;
         cg->beta = 0.0;

@@ -192,6 +192,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
         cg->done = CG_CONVERGED;
     } else if (it >= cg->max_it) {
         cg->done = CG_MAXIT;
+    } else if (cg->stag_window > 0) {
+        if (rr < cg->rr_min) {
+            cg->rr_min = rr;
+            cg->it_min = it;
+        } else if (it - cg->it_min >= cg->stag_window) {
+            cg->done = CG_STAGNATED;
+        }
     }
 }
 

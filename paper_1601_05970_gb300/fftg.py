@@ -64,7 +64,8 @@ class fftg_stats(C.Structure):
                 ("cg_per_newton", C.c_int * FFTG_MAX_NEWTON_LOG),
                 ("newton_norm", C.c_double * FFTG_MAX_NEWTON_LOG),
                 ("residual", C.c_double * FFTG_MAX_NEWTON_LOG),
-                ("cg_relres", C.c_double * FFTG_MAX_NEWTON_LOG)]
+                ("cg_relres", C.c_double * FFTG_MAX_NEWTON_LOG),
+                ("cg_status", C.c_int * FFTG_MAX_NEWTON_LOG)]
 
 
 # every symbol include/fftg.h declares, with its ctypes signature
@@ -203,7 +204,7 @@ class Cell:
         return dict(status=s.status, newton_iters=s.newton_iters, cg_iters=s.cg_iters,
                     cg_per_newton=list(s.cg_per_newton[:n]),
                     newton_norm=list(s.newton_norm[:n]), residual=list(s.residual[:n]),
-                    cg_relres=list(s.cg_relres[:n]))
+                    cg_relres=list(s.cg_relres[:n]), cg_status=list(s.cg_status[:n]))
 
     def tangent(self, tol_cg):
         out = np.zeros(36)
