@@ -110,6 +110,7 @@ struct Prof {
 struct fftg_handle {
     int N = 0;
     long long V = 0;
+    long long cs = 0;            // component stride of the fields (padded)
     int H = 0;
     int mixed = 1;
     int nrhs = 6;
@@ -204,8 +205,16 @@ struct Layout {
         off_partials, off_cg, off_nd, off_out36, total;
 };
 
+// Component stride of every field: N^3 rounded up past N^3 + 4 to a
+// multiple of 32 elements, so each component starts 128-byte aligned and a
+// 16-byte vector that straddles the end of the grid stays in the padding.
+long long comp_stride(int N) {
+    const long long V = (long long)N * N * N;
+    return ((V + 4 + 31) / 32) * 32;
+}
+
 Layout make_layout(int N, int mixed, int nrhs) {
-    const size_t V = (size_t)N * N * N;
+    const size_t V = (size_t)comp_stride(N);
     const size_t H = (size_t)(N + 1) / 2;
     const size_t ts = mixed ? 4 : 8;
     const size_t nf = (size_t)std::max(1, nrhs);
@@ -220,7 +229,7 @@ Layout make_layout(int N, int mixed, int nrhs) {
         o += align256(bytes);
         return at;
     };
-    L.off_phase = take(V);
+    L.off_phase = take((size_t)N * N * N);
     L.off_mats = take(256 * 4 * 8);
     L.off_eps_star = take(6 * V * 8);
     L.off_eps_work = take(6 * V * 8);
@@ -285,6 +294,7 @@ static int launch_constitutive(fftg_handle* h, const double E[6], const double* 
                                bool write_history, CGState* cg, bool write_tangent = true) {
     ConstArgs a{};
     a.V = h->V;
+    a.cs = h->cs;
     for (int c = 0; c < 6; ++c) a.E[c] = E[c];
     a.eps = eps;
     a.eps_p = h->eps_p[h->hist];
@@ -314,10 +324,21 @@ static PassArgs base_args(fftg_handle* h, bool fp64) {
     PassArgs a{};
     a.tw = fp64 ? h->tw64 : h->tw32;
     a.partials = h->partials;
-    a.fstride = 6 * h->V;
+    a.cs = h->cs;
+    a.fstride = 6 * h->cs;
     a.sstride = 6LL * h->N * h->N * h->H;
     a.tstride = 0;
     return a;
+}
+
+// Copy a [6][V] field between a caller layout (component stride V) and the
+// padded internal layout (component stride cs).
+static cudaError_t copy_field(fftg_handle* h, void* dst, bool dst_padded, const void* src,
+                              bool src_padded, size_t elem, cudaMemcpyKind kind, int ncomp = 6) {
+    const size_t w = (size_t)h->V * elem;
+    const size_t dp = (dst_padded ? (size_t)h->cs : (size_t)h->V) * elem;
+    const size_t sp = (src_padded ? (size_t)h->cs : (size_t)h->V) * elem;
+    return cudaMemcpy2DAsync(dst, dp, src, sp, w, ncomp, kind, h->stream);
 }
 
 // Forward-project-inverse core on the spectrum buffer (P2, P3, P4).
@@ -346,7 +367,7 @@ static int launch_residual(fftg_handle* h) {
     b.out = h->r;
     b.cg = h->cg;
     CK(pass(h, h->mixed ? PK_P5_RHS_F64_TO_F32 : PK_P5_RHS_F64_TO_F64, b, 1));
-    CK(cudaMemsetAsync(h->x, 0, 6 * h->V * (h->mixed ? 4 : 8), h->stream));
+    CK(cudaMemsetAsync(h->x, 0, 6 * h->cs * (h->mixed ? 4 : 8), h->stream));
     return FFTG_OK;
 }
 
@@ -371,14 +392,15 @@ static int launch_cg_iteration(fftg_handle* h, int nf) {
     CK(pass(h, f64 ? PK_P5_DOT_F64 : PK_P5_DOT_F32, b, nf));
     VecArgs u{};
     u.V = h->V;
+    u.cs = h->cs;
     u.x = h->x;
     u.r = h->r;
     u.p = h->p;
     u.q = h->q;
     u.cg = h->cg;
     u.partials = h->partials;
-    u.fstride = 6 * h->V;
-    dim3 g(pointwise_blocks(h->V), 1, nf);
+    u.fstride = 6 * h->cs;
+    dim3 g(vector_blocks(h->cs, f64 ? 8 : 4), 1, nf);
     const int slot = prof_begin(h, f64 ? KK_CG_UPDATE_F64 : KK_CG_UPDATE_F32);
     if (f64)
         k_cg_update<double><<<g, kThreads, 0, h->stream>>>(u);
@@ -476,6 +498,7 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
     if (!h) return FFTG_ENOMEM;
     h->N = N;
     h->V = (long long)V;
+    h->cs = comp_stride(N);
     h->H = (N + 1) / 2;
     h->mixed = o.precision == FFTG_MIXED;
     h->nrhs = o.nrhs_tangent;
@@ -546,8 +569,8 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
         cudaMemcpyAsync(h->mats, m.data(), m.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw64, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw32, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(h->eps_star, 0, 6 * V * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(h->eps_p[0], 0, 6 * V * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->eps_star, 0, 6 * h->cs * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->eps_p[0], 0, 6 * h->cs * 8, s) != cudaSuccess ||
         cudaMemsetAsync(h->epbar[0], 0, V * 8, s) != cudaSuccess ||
         cudaMemsetAsync(h->cg, 0, 6 * sizeof(CGState), s) != cudaSuccess ||
         cudaMemsetAsync(h->nd, 0, sizeof(NewtonDev), s) != cudaSuccess ||
@@ -633,7 +656,7 @@ int fftg_step(fftg_handle* h, const double dE[6], double tol_newton, double tol_
     for (int c = 0; c < 6; ++c) Et[c] = h->E[c] + dE[c];
     const double normE = std::sqrt((double)h->V) * frob6(Et);
     const double tol_inner = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
-    CK(cudaMemcpyAsync(h->eps_work, h->eps_star, 6 * h->V * 8, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->eps_work, h->eps_star, 6 * h->cs * 8, cudaMemcpyDeviceToDevice, h->stream));
     h->have_tangent = false;
     int it = 0;
     bool converged = false;
@@ -649,6 +672,7 @@ int fftg_step(fftg_handle* h, const double dE[6], double tol_newton, double tol_
         if (rc) return rc;
         VecArgs u{};
         u.V = h->V;
+        u.cs = h->cs;
         u.x = h->x;
         u.eps = h->eps_work;
         u.nd = h->nd;
@@ -731,11 +755,12 @@ int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters)
     CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
     VecArgs u{};
     u.V = h->V;
+    u.cs = h->cs;
     u.tangent = h->tangent;
     u.cg = h->cg;
     u.nd = h->nd;
     u.partials = h->partials;
-    u.fstride = 6 * h->V;
+    u.fstride = 6 * h->cs;
     const int nb = pointwise_blocks(h->V);
     int slot = prof_begin(h, KK_TANGENT_FLOOR);
     if (f64)
@@ -756,7 +781,7 @@ int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters)
     b.out = h->r;
     b.cg = h->cg;
     CK(pass(h, f64 ? PK_P5_RHS_F64_TO_F64 : PK_P5_RHS_F32_TO_F32, b, 6));
-    CK(cudaMemsetAsync(h->x, 0, 6 * 6 * h->V * (h->mixed ? 4 : 8), h->stream));
+    CK(cudaMemsetAsync(h->x, 0, 6 * 6 * h->cs * (h->mixed ? 4 : 8), h->stream));
     rc = run_cg(h, 6);
     if (rc) return rc;
     int total = 0;
@@ -789,8 +814,8 @@ int fftg_get_state(fftg_handle* h, void* buf, size_t bytes) {
     if (!h || !buf || bytes < fftg_state_bytes(h)) return FFTG_EINVAL;
     double* d = (double*)buf;
     std::memcpy(d, h->E, 6 * sizeof(double));
-    CK(cudaMemcpyAsync(d + 6, h->eps_star, 6 * h->V * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(d + 6 + 6 * h->V, h->eps_p[h->hist], 6 * h->V * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(copy_field(h, d + 6, false, h->eps_star, true, 8, cudaMemcpyDeviceToHost));
+    CK(copy_field(h, d + 6 + 6 * h->V, false, h->eps_p[h->hist], true, 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpyAsync(d + 6 + 12 * h->V, h->epbar[h->hist], h->V * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return FFTG_OK;
@@ -801,8 +826,8 @@ int fftg_set_state(fftg_handle* h, const void* buf, size_t bytes) {
     const double* d = (const double*)buf;
     for (int c = 0; c < 6; ++c)
         if (!std::isfinite(d[c])) return FFTG_EINVAL;
-    CK(cudaMemcpyAsync(h->eps_star, d + 6, 6 * h->V * 8, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->eps_p[h->hist], d + 6 + 6 * h->V, 6 * h->V * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(copy_field(h, h->eps_star, true, d + 6, false, 8, cudaMemcpyHostToDevice));
+    CK(copy_field(h, h->eps_p[h->hist], true, d + 6 + 6 * h->V, false, 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpyAsync(h->epbar[h->hist], d + 6 + 12 * h->V, h->V * 8, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     std::memcpy(h->E, d, 6 * sizeof(double));
@@ -815,7 +840,7 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
     const size_t V = (size_t)h->V;
     switch (which) {
         case FFTG_FIELD_STRAIN: {
-            CK(cudaMemcpyAsync(out, h->eps_star, 6 * V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(copy_field(h, out, false, h->eps_star, true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             for (int c = 0; c < 6; ++c)
                 for (size_t v = 0; v < V; ++v) out[c * V + v] += h->E[c];
@@ -828,7 +853,7 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
             // increment is left untouched.
             int rc = launch_constitutive(h, h->E, h->eps_star, h->sigma, false, nullptr, false);
             if (rc) return rc;
-            CK(cudaMemcpyAsync(out, h->sigma, 6 * V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(copy_field(h, out, false, h->sigma, true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
         }
@@ -837,7 +862,7 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
         case FFTG_FIELD_EPS_P:
-            CK(cudaMemcpyAsync(out, h->eps_p[h->hist], 6 * V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(copy_field(h, out, false, h->eps_p[h->hist], true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
         default:
@@ -848,17 +873,24 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
 int fftg_op_project(fftg_handle* h, int precision, const void* tau, void* out) {
     if (!h || !tau || !out || (precision != FFTG_FP64 && precision != FFTG_MIXED)) return FFTG_EINVAL;
     const bool f64 = precision == FFTG_FP64;
+    const size_t es = f64 ? 8 : 4;
+    // internal scratch in the padded layout: FP64 in sigma / eps_work, FP32
+    // in p / q (these hold no state between increments)
+    void* in_buf = f64 ? (void*)h->sigma : h->p;
+    void* out_buf = f64 ? (void*)h->eps_work : h->q;
+    CK(copy_field(h, in_buf, true, tau, false, es, cudaMemcpyDeviceToDevice));
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     PassArgs a = base_args(h, f64);
-    a.in = tau;
+    a.in = in_buf;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_PLAIN_F64 : PK_P1_PLAIN_F32, a, 1));
     int rc = run_p234(h, f64, invN3, nullptr, 1);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
-    b.out = out;
+    b.out = out_buf;
     CK(pass(h, f64 ? PK_P5_PLAIN_F64 : PK_P5_PLAIN_F32, b, 1));
+    CK(copy_field(h, out, false, out_buf, true, es, cudaMemcpyDeviceToDevice));
     return FFTG_OK;
 }
 
@@ -866,8 +898,14 @@ int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps, 
     if (!h) return FFTG_EINVAL;
     double Et[6];
     for (int c = 0; c < 6; ++c) Et[c] = h->E[c] + (dE ? dE[c] : 0.0);
-    int rc = launch_constitutive(h, Et, eps ? eps : h->eps_star, sigma ? sigma : h->sigma, false, nullptr);
+    const double* e = h->eps_star;
+    if (eps) {
+        CK(copy_field(h, h->eps_work, true, eps, false, 8, cudaMemcpyDeviceToDevice));
+        e = h->eps_work;
+    }
+    int rc = launch_constitutive(h, Et, e, h->sigma, false, nullptr);
     if (rc) return rc;
+    if (sigma) CK(copy_field(h, sigma, false, h->sigma, true, 8, cudaMemcpyDeviceToDevice));
     h->have_tangent = false;
     return FFTG_OK;
 }
@@ -876,12 +914,14 @@ int fftg_op_matvec(fftg_handle* h, int precision, const void* p, void* q, double
     if (!h || !p || !q) return FFTG_EINVAL;
     const bool f64 = precision == FFTG_FP64;
     if (f64 == (bool)h->mixed) return FFTG_EINVAL;  // must match the tangent's precision
+    const size_t es = f64 ? 8 : 4;
     set_cg_params(h, 1, 1.0);
     h->h_cg[0].rr = 1.0;
     CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+    CK(copy_field(h, h->p, true, p, false, es, cudaMemcpyDeviceToDevice));
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     PassArgs a = base_args(h, f64);
-    a.in = p;
+    a.in = h->p;
     a.tangent = h->tangent;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_TAN_F64 : PK_P1_TAN_F32, a, 1));
@@ -889,10 +929,11 @@ int fftg_op_matvec(fftg_handle* h, int precision, const void* p, void* q, double
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
-    b.out = q;
-    b.aux = p;
+    b.out = h->q;
+    b.aux = h->p;
     b.cg = h->cg;
     CK(pass(h, f64 ? PK_P5_DOT_F64 : PK_P5_DOT_F32, b, 1));
+    CK(copy_field(h, q, false, h->q, true, es, cudaMemcpyDeviceToDevice));
     if (pq) {
         CK(cudaMemcpyAsync(h->h_cg, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));

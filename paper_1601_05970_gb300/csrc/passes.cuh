@@ -34,6 +34,8 @@ struct PassArgs {
     double* partials;      // [nf][nblocks][2]
     const void* tw;        // w_N^j, j < N, in the FFT precision
     double scale;          // P3: factor on Ghat (+-1/N^3)
+    long long cs;          // component stride of real fields and of the tangent
+                           // (elements; >= N^3 + 4, a multiple of 32)
     long long fstride;     // real-field stride between fields (elements)
     long long sstride;     // spectrum stride between fields (complex elements)
     long long tstride;     // tangent stride between fields (0: shared)
@@ -44,13 +46,28 @@ struct Cfg {
     static constexpr int H = (N + 1) / 2;
     static constexpr int CS = (int)sizeof(cplx<T>);
     static constexpr int BUDGET = 100 * 1024;
+    static constexpr int ROW_BUDGET = 50 * 1024;
     static constexpr int fl2(int x) {
         return x >= 64 ? 64 : x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1;
     }
-    static constexpr int R = fl2(BUDGET / (3 * N * CS));                      // rows, P1/P5
+    // rows per block in P1/P5: a power of two >= 4, so that a block's rows
+    // are a whole number of 16-byte vectors
+    static constexpr int R0 = fl2(ROW_BUDGET / (3 * N * CS));
+    static constexpr int R = R0 < 4 ? 4 : R0;
+    static constexpr int VW = 16 / (int)sizeof(T);  // elements per 16-byte vector
     static constexpr int W3 = fl2(BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(BUDGET / (6 * N * CS));
     static constexpr int W2 = (CS == 8) ? 32 : 16;                            // columns, P2/P4
     static constexpr int S2 = fl2(BUDGET / (N * W2 * CS)) > 16 ? 16 : fl2(BUDGET / (N * W2 * CS));
+    static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
+    static constexpr int cap(int x) { return x > 1024 ? 1024 : x; }
+    // threads of the column passes: one stage-A item per thread
+    static constexpr int T2 = cap(rup32(S2 * W2 * Plan<N>::N2));
+    // P3: one stage-A item per thread, and at least two per (column, k1)
+    // pair in the fused middle stage
+    static constexpr int T3a = rup32(6 * W3 * Plan<N>::N2);
+    static constexpr int T3b = rup32(2 * W3 * Plan<N>::N1);
+    // single-stage plans (N2 = 1) loop over the middle stage with 256 threads
+    static constexpr int T3 = Plan<N>::N2 == 1 ? (T3a > 256 ? cap(T3a) : 256) : cap(T3a > T3b ? T3a : T3b);
     static constexpr size_t smem_rows = (size_t)(3 * R * N + N) * CS;
     static constexpr size_t smem_p3 = (size_t)(6 * W3 * N + N) * CS;
     static constexpr size_t smem_p24 = (size_t)(S2 * W2 * N + N) * CS;
@@ -60,17 +77,14 @@ struct Cfg {
 template <typename T>
 __device__ __forceinline__ void load_tw(cplx<T>* tw, const void* src, int n) {
     const cplx<T>* s = (const cplx<T>*)src;
-    for (int i = threadIdx.x; i < n; i += kThreads) tw[i] = s[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = s[i];
 }
 
 // s = C : p with the compact J2 tangent (Section 4.2):
 // C = K I(x)I + 2G_eff I_d - w (x) w,  w = sqrt(-b) N, b < 0
 template <typename T>
-__device__ __forceinline__ void apply_tangent(const T* __restrict__ tg, long long v, long long V,
-                                              const T (&p)[6], T (&s)[6]) {
-    const T K = tg[v], g2 = tg[V + v];
-    const T w0 = tg[2 * V + v], w1 = tg[3 * V + v], w3 = tg[4 * V + v], w4 = tg[5 * V + v],
-            w5 = tg[6 * V + v];
+__device__ __forceinline__ void apply_tangent7(T K, T g2, T w0, T w1, T w3, T w4, T w5,
+                                               const T (&p)[6], T (&s)[6]) {
     const T w2 = -(w0 + w1);
     const T tr = p[0] + p[1] + p[2];
     const T m = tr * T(1.0 / 3.0);
@@ -82,6 +96,37 @@ __device__ __forceinline__ void apply_tangent(const T* __restrict__ tg, long lon
     s[3] = g2 * p[3] - wp * w3;
     s[4] = g2 * p[4] - wp * w4;
     s[5] = g2 * p[5] - wp * w5;
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+
+// 16-byte vector load/store of VW consecutive elements
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&v)[16 / sizeof(T)]) {
+    using VT = typename Vec16<T>::type;
+    const VT t = *reinterpret_cast<const VT*>(p);
+    static_assert(sizeof(VT) == 16, "16-byte vectors");
+    const T* e = reinterpret_cast<const T*>(&t);
+#pragma unroll
+    for (int k = 0; k < (int)(16 / sizeof(T)); ++k) v[k] = e[k];
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&v)[16 / sizeof(T)]) {
+    using VT = typename Vec16<T>::type;
+    VT t;
+    T* e = reinterpret_cast<T*>(&t);
+#pragma unroll
+    for (int k = 0; k < (int)(16 / sizeof(T)); ++k) e[k] = v[k];
+    *reinterpret_cast<VT*>(p) = t;
 }
 
 // ----------------------------------------------------------------------- P1
@@ -97,11 +142,11 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
     if (MODE == P1_CG && a.cg[f].done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
-    const long long V = (long long)N * N * N;
     const int row0 = blockIdx.x * R;
     const int nrows = min(R, N * N - row0);
     const long long base = (long long)row0 * N;
     const int nel = nrows * N;
+    const long long cs = a.cs;
     const T* in = (const T*)a.in + f * a.fstride;
     const T* tg = (const T*)a.tangent + f * a.tstride;
     T beta = T(0);
@@ -110,37 +155,72 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
         beta = (T)a.cg[f].beta;
         first = a.cg[f].it == 0;
     }
-    for (int i = tid; i < R * N; i += kThreads) {
-        T s[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        if (i < nel) {
-            const long long v = base + i;
-            T p[6];
+    // Elementwise phase on 16-byte vectors. A block's R rows are R*N
+    // contiguous elements per component starting at a multiple of VW; in the
+    // last block the vector that straddles the end of the grid reads and
+    // writes only the padding of the component (cs >= N^3 + 4), and its
+    // lanes past the grid belong to rows that the FFT stages skip.
+    constexpr int VW = C::VW;
+    for (int j = tid; j < (R * N) / VW; j += kThreads) {
+        const int i0 = j * VW;
+        T s[6][VW];
+        if (i0 < nel) {
+            const long long v0 = base + i0;
+            T p[6][VW];
             if (MODE == P1_CG) {
                 const T* r = (const T*)a.aux + f * a.fstride;
                 T* pp = (T*)a.aux2 + f * a.fstride;
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    const T pv = first ? r[c * V + v] : r[c * V + v] + beta * pp[c * V + v];
-                    pp[c * V + v] = pv;
-                    p[c] = pv;
+                    ld16<T>(r + c * cs + v0, p[c]);
+                    if (!first) {
+                        T po[VW];
+                        ld16<T>(pp + c * cs + v0, po);
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) p[c][e] += beta * po[e];
+                    }
+                    st16<T>(pp + c * cs + v0, p[c]);
                 }
             } else if (MODE == P1_TANRHS) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) p[c] = (c == f) ? T(1) : T(0);
+                for (int c = 0; c < 6; ++c)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) p[c][e] = (c == f) ? T(1) : T(0);
             } else {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) p[c] = in[c * V + v];
+                for (int c = 0; c < 6; ++c) ld16<T>(in + c * cs + v0, p[c]);
             }
             if (MODE == P1_PLAIN) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) s[c] = p[c];
+                for (int c = 0; c < 6; ++c)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) s[c][e] = p[c][e];
             } else {
-                apply_tangent<T>(tg, v, V, p, s);
+                T t7[7][VW];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) ld16<T>(tg + k * cs + v0, t7[k]);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const T pe[6] = {p[0][e], p[1][e], p[2][e], p[3][e], p[4][e], p[5][e]};
+                    T se[6];
+                    apply_tangent7<T>(t7[0][e], t7[1][e], t7[2][e], t7[3][e], t7[4][e], t7[5][e],
+                                      t7[6][e], pe, se);
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) s[c][e] = se[c];
+                }
             }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) s[c][e] = T(0);
         }
-        z[i] = mk(s[0], s[1]);
-        z[R * N + i] = mk(s[2], s[3]);
-        z[2 * R * N + i] = mk(s[4], s[5]);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            z[i0 + e] = mk(s[0][e], s[1][e]);
+            z[R * N + i0 + e] = mk(s[2][e], s[3][e]);
+            z[2 * R * N + i0 + e] = mk(s[4][e], s[5][e]);
+        }
     }
     __syncthreads();
     constexpr int NP = 3 * R;
@@ -176,10 +256,12 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
 }
 
 // -------------------------------------------------------------- P2 / P4 (x2)
+// Blocks of T2 = (slabs x columns x N2) threads: stage A is one item per
+// thread; stage B takes N1/N2 rounds.
 template <int N, typename T, bool FWD>
-__global__ void __launch_bounds__(kThreads) k_p24(PassArgs a) {
+__global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
     using C = Cfg<N, T>;
-    constexpr int H = C::H, W = C::W2, S = C::S2;
+    constexpr int H = C::H, W = C::W2, S = C::S2, NT = C::T2;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -193,28 +275,28 @@ __global__ void __launch_bounds__(kThreads) k_p24(PassArgs a) {
     cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
     constexpr int P = S * W;
     if (FWD) {
-        for (int it = tid; it < P * N2; it += kThreads) {
+        for (int it = tid; it < P * N2; it += NT) {
             const int pc = it % P, t = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < 6 * N)
                 fwdA<N, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, t, tw);
         }
         __syncthreads();
-        for (int it = tid; it < P * N1; it += kThreads) {
+        for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < 6 * N)
                 fwdB<N, true, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, k1, tw);
         }
     } else {
-        for (int it = tid; it < P * N1; it += kThreads) {
+        for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < 6 * N)
                 invB<N, true, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, k1, tw);
         }
         __syncthreads();
-        for (int it = tid; it < P * N2; it += kThreads) {
+        for (int it = tid; it < P * N2; it += NT) {
             const int pc = it % P, t = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < 6 * N)
@@ -252,10 +334,16 @@ __device__ __forceinline__ void apply_ghat(cplx<T>* b, int cs, int f1, int f2, i
 }
 
 // ------------------------------------------------------------- P3 (x1 + Ghat)
+// Stage A forward (global -> shared), then one fused register stage per
+// (column, k1): the N2-point forward DFT of the six components, Ghat at the
+// N2 frequencies k1 + N1*k2, the N2-point inverse DFT and its twiddle, back
+// in place; then stage A inverse (shared -> global). Two adjacent lanes share
+// a (column, k1): lane 0 holds the normal components (11, 22, 33), lane 1
+// the shear ones (23, 13, 12); they exchange their parts of tau n by shuffle.
 template <int N, typename T>
-__global__ void __launch_bounds__(kThreads) k_p3(PassArgs a) {
+__global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T3 <= 512) ? 2 : 1) k_p3(PassArgs a) {
     using C = Cfg<N, T>;
-    constexpr int H = C::H, W = C::W3;
+    constexpr int H = C::H, W = C::W3, NT = C::T3;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -265,46 +353,86 @@ __global__ void __launch_bounds__(kThreads) k_p3(PassArgs a) {
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
     __syncthreads();
-    const int col0 = blockIdx.x * W, k2 = blockIdx.y;
+    const int col0 = blockIdx.x * W, k2g = blockIdx.y;
     cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
     constexpr int P = 6 * W;
     const long long NH = (long long)N * H;
-    for (int it = tid; it < P * N2; it += kThreads) {
+    for (int it = tid; it < P * N2; it += NT) {
         const int pc = it % P, t = it / P;
         const int c = pc / W, w = pc - c * W, col = col0 + w;
-        if (col < H) fwdA<N, T>(sp + c * N * NH + k2 * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
+        if (col < H) fwdA<N, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
     }
     __syncthreads();
-    if (N2 > 1) {
-        for (int it = tid; it < P * N1; it += kThreads) {
-            const int pc = it % P, k1 = it / P;
-            const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+    const T scale = (T)a.scale;
+    const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
+    // Uniform loop: every lane of every warp runs the same iterations and
+    // the shuffles; lanes without a valid item compute on zeros and store
+    // nothing.
+    for (int it0 = 0; it0 < 2 * W * N1; it0 += NT) {
+        const int it = it0 + tid;
+        const int half = it & 1, pair = it >> 1;
+        const int w = pair % W, k1 = (pair / W) % N1, col = col0 + w;
+        const bool valid = (it < 2 * W * N1) && (col < H);
+        cplx<T> v[3][N2];
+        cplx<T>* b = buf + (3 * half) * N * W + w;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int q = 0; q < N2; ++q)
+                v[c][q] = valid ? b[c * N * W + (N2 * k1 + q) * W] : mk(T(0), T(0));
+            if (N2 > 1) RegDFT<N, N2, -1, T>::run(v[c], tw);
         }
-        __syncthreads();
-    }
-    const int f2 = (k2 <= (N - 1) / 2) ? k2 : k2 - N;
-    for (int it = tid; it < N * W; it += kThreads) {
-        const int pos = it / W, w = it - pos * W, col = col0 + w;
-        if (col < H) {
-            const int kk = (pos / N2) + N1 * (pos % N2);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const int kk = k1 + N1 * k2;
             const int f1 = (kk <= (N - 1) / 2) ? kk : kk - N;
-            apply_ghat<T>(buf + pos * W + w, N * W, f1, f2, col, (T)a.scale);
+            const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(col) * T(col);
+            const T inv = q2 > T(0) ? T(1) / sqrt(q2) : T(0);
+            const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(col) * inv;
+            // partial tau n: normals (lane 0) or shears (lane 1)
+            cplx<T> u0, u1, u2;
+            if (half == 0) {
+                u0 = n0 * v[0][k2];
+                u1 = n1 * v[1][k2];
+                u2 = n2 * v[2][k2];
+            } else {  // v[0] = 23, v[1] = 13, v[2] = 12
+                u0 = n1 * v[2][k2] + n2 * v[1][k2];
+                u1 = n0 * v[2][k2] + n2 * v[0][k2];
+                u2 = n0 * v[1][k2] + n1 * v[0][k2];
+            }
+            const cplx<T> t0 = mk(__shfl_xor_sync(0xffffffffu, u0.x, 1), __shfl_xor_sync(0xffffffffu, u0.y, 1));
+            const cplx<T> t1 = mk(__shfl_xor_sync(0xffffffffu, u1.x, 1), __shfl_xor_sync(0xffffffffu, u1.y, 1));
+            const cplx<T> t2 = mk(__shfl_xor_sync(0xffffffffu, u2.x, 1), __shfl_xor_sync(0xffffffffu, u2.y, 1));
+            const cplx<T> t0s = u0 + t0, t1s = u1 + t1, t2s = u2 + t2;  // tau n
+            const cplx<T> sn = n0 * t0s + n1 * t1s + n2 * t2s;           // n . tau n
+            if (half == 0) {
+                v[0][k2] = scale * (T(2) * n0 * t0s - (n0 * n0) * sn);
+                v[1][k2] = scale * (T(2) * n1 * t1s - (n1 * n1) * sn);
+                v[2][k2] = scale * (T(2) * n2 * t2s - (n2 * n2) * sn);
+            } else {
+                v[0][k2] = scale * (n1 * t2s + n2 * t1s - (n1 * n2) * sn);
+                v[1][k2] = scale * (n0 * t2s + n2 * t0s - (n0 * n2) * sn);
+                v[2][k2] = scale * (n0 * t1s + n1 * t0s - (n0 * n1) * sn);
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (N2 > 1) RegDFT<N, N2, +1, T>::run(v[c], tw);
+#pragma unroll
+                for (int t = 0; t < N2; ++t) {
+                    cplx<T> z = v[c][t];
+                    if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[(t * k1) % N]);
+                    b[c * N * W + (N2 * k1 + t) * W] = z;
+                }
+            }
         }
     }
     __syncthreads();
-    if (N2 > 1) {
-        for (int it = tid; it < P * N1; it += kThreads) {
-            const int pc = it % P, k1 = it / P;
-            const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
-        }
-        __syncthreads();
-    }
-    for (int it = tid; it < P * N2; it += kThreads) {
+    for (int it = tid; it < P * N2; it += NT) {
         const int pc = it % P, t = it / P;
         const int c = pc / W, w = pc - c * W, col = col0 + w;
-        if (col < H) invA<N, T>(buf + c * N * W + w, W, sp + c * N * NH + k2 * H + col, (int)NH, t, tw);
+        if (col < H) invA<N, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, t, tw);
     }
 }
 
@@ -324,7 +452,6 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
     if (MODE == P5_DOT && cg->done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
-    const long long V = (long long)N * N * N;
     const int row0 = blockIdx.x * R;
     const int nrows = min(R, N * N - row0);
     const long long base = (long long)row0 * N;
@@ -357,34 +484,56 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
         if (pc % R < nrows) invA<N, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
     }
     __syncthreads();
+    const long long cs = a.cs;
     TO* out = (TO*)a.out + f * a.fstride;
     T acc0 = T(0);
     double acc1 = 0.0;
-    for (int i = tid; i < nel; i += kThreads) {
-        const long long v = base + i;
-        const cplx<T> z0 = z[i], z1 = z[R * N + i], z2 = z[2 * R * N + i];
-        const T q[6] = {z0.x, z0.y, z1.x, z1.y, z2.x, z2.y};
+    // Vectors of VO output elements (16 bytes of TO); lanes past the grid in
+    // the last block write only component padding and are left out of the
+    // sums.
+    constexpr int VO = 16 / (int)sizeof(TO);
+    for (int j = tid; j < (R * N) / VO; j += kThreads) {
+        const int i0 = j * VO;
+        if (i0 >= nel) continue;
+        const long long v0 = base + i0;
+        TO q[6][VO];
+#pragma unroll
+        for (int e = 0; e < VO; ++e) {
+            const cplx<T> z0 = z[i0 + e], z1 = z[R * N + i0 + e], z2 = z[2 * R * N + i0 + e];
+            q[0][e] = (TO)z0.x;
+            q[1][e] = (TO)z0.y;
+            q[2][e] = (TO)z1.x;
+            q[3][e] = (TO)z1.y;
+            q[4][e] = (TO)z2.x;
+            q[5][e] = (TO)z2.y;
+            if (MODE == P5_RHS && i0 + e < nel) {
+                const T qd[6] = {z0.x, z0.y, z1.x, z1.y, z2.x, z2.y};
+                acc1 += (double)frob<T>(qd, qd);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) st16<TO>(out + c * cs + v0, q[c]);
         if (MODE == P5_DOT) {
-            const T* p = (const T*)a.aux + f * a.fstride;
-            T pv[6];
+            const TO* p = (const TO*)a.aux + f * a.fstride;
+            TO pv[6][VO];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                out[c * V + v] = (TO)q[c];
-                pv[c] = p[c * V + v];
+            for (int c = 0; c < 6; ++c) ld16<TO>(p + c * cs + v0, pv[c]);
+#pragma unroll
+            for (int e = 0; e < VO; ++e) {
+                if (i0 + e < nel) {
+                    const TO pe[6] = {pv[0][e], pv[1][e], pv[2][e], pv[3][e], pv[4][e], pv[5][e]};
+                    const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
+                    acc0 += (T)frob<TO>(pe, qe);
+                }
             }
-            acc0 += frob<T>(pv, q);
         } else if (MODE == P5_RHS) {
-            TO r[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                r[c] = (TO)q[c];
-                out[c * V + v] = r[c];
+            for (int e = 0; e < VO; ++e) {
+                if (i0 + e < nel) {
+                    const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
+                    acc0 += (T)frob<TO>(qe, qe);
+                }
             }
-            acc1 += (double)frob<T>(q, q);
-            acc0 += (T)frob<TO>(r, r);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) out[c * V + v] = (TO)q[c];
         }
     }
     if (MODE == P5_PLAIN) return;
@@ -451,11 +600,12 @@ template <int N>
 cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s);
 
 template <typename K>
-static cudaError_t launch_k(K kernel, dim3 grid, size_t smem, const PassArgs& a, cudaStream_t s) {
+static cudaError_t launch_k(K kernel, dim3 grid, size_t smem, const PassArgs& a, cudaStream_t s,
+                            int threads = kThreads) {
     static_assert(sizeof(PassArgs) < 4096, "kernel params");
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kernel<<<grid, kThreads, smem, s>>>(a);
+    kernel<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -477,12 +627,12 @@ cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s)
         case PK_P1_CG_F32: return launch_k(k_p1<N, float, P1_CG>, r32, C32::smem_rows, a, s);
         case PK_P1_TANRHS_F64: return launch_k(k_p1<N, double, P1_TANRHS>, r64, C64::smem_rows, a, s);
         case PK_P1_TANRHS_F32: return launch_k(k_p1<N, float, P1_TANRHS>, r32, C32::smem_rows, a, s);
-        case PK_P2_F64: return launch_k(k_p24<N, double, true>, c64, C64::smem_p24, a, s);
-        case PK_P2_F32: return launch_k(k_p24<N, float, true>, c32, C32::smem_p24, a, s);
-        case PK_P4_F64: return launch_k(k_p24<N, double, false>, c64, C64::smem_p24, a, s);
-        case PK_P4_F32: return launch_k(k_p24<N, float, false>, c32, C32::smem_p24, a, s);
-        case PK_P3_F64: return launch_k(k_p3<N, double>, g64, C64::smem_p3, a, s);
-        case PK_P3_F32: return launch_k(k_p3<N, float>, g32, C32::smem_p3, a, s);
+        case PK_P2_F64: return launch_k(k_p24<N, double, true>, c64, C64::smem_p24, a, s, C64::T2);
+        case PK_P2_F32: return launch_k(k_p24<N, float, true>, c32, C32::smem_p24, a, s, C32::T2);
+        case PK_P4_F64: return launch_k(k_p24<N, double, false>, c64, C64::smem_p24, a, s, C64::T2);
+        case PK_P4_F32: return launch_k(k_p24<N, float, false>, c32, C32::smem_p24, a, s, C32::T2);
+        case PK_P3_F64: return launch_k(k_p3<N, double>, g64, C64::smem_p3, a, s, C64::T3);
+        case PK_P3_F32: return launch_k(k_p3<N, float>, g32, C32::smem_p3, a, s, C32::T3);
         case PK_P5_PLAIN_F64: return launch_k(k_p5<N, double, P5_PLAIN, double>, r64, C64::smem_rows, a, s);
         case PK_P5_PLAIN_F32: return launch_k(k_p5<N, float, P5_PLAIN, float>, r32, C32::smem_rows, a, s);
         case PK_P5_DOT_F64: return launch_k(k_p5<N, double, P5_DOT, double>, r64, C64::smem_rows, a, s);

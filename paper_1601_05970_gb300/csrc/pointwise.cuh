@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "passes.cuh"
 
 namespace fftg {
 
@@ -17,8 +18,17 @@ inline int pointwise_blocks(long long V) {
     return (int)(b < kMaxPointwiseBlocks ? b : kMaxPointwiseBlocks);
 }
 
+// Grid of the vectorised CG update: one thread per 16-byte vector up to a
+// fixed cap (depends only on the grid size).
+inline int vector_blocks(long long cs, int elem_bytes) {
+    const long long nv = cs / (16 / elem_bytes);
+    long long b = (nv + kThreads - 1) / kThreads;
+    return (int)(b < 2432 ? b : 2432);
+}
+
 struct ConstArgs {
     long long V;
+    long long cs;            // component stride of the fields (>= V)
     double E[6];
     const double* eps;       // [6][V] fluctuation eps*
     const double* eps_p;     // [6][V] committed plastic strain
@@ -43,7 +53,7 @@ struct ConstArgs {
 // stored as K, 2G_eff, w = sqrt(-b) N (b the N(x)N coefficient, negative).
 template <typename TT>
 __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
-    const long long V = a.V;
+    const long long V = a.V, cs = a.cs;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     TT* tg = (TT*)a.tangent;
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
@@ -54,8 +64,8 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
         double e[6], ep[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            ep[c] = a.eps_p[c * V + v];
-            e[c] = a.E[c] + a.eps[c * V + v] - ep[c];
+            ep[c] = a.eps_p[c * cs + v];
+            e[c] = a.E[c] + a.eps[c * cs + v] - ep[c];
         }
         const double eb = a.epbar[v];
         const double tr = e[0] + e[1] + e[2];
@@ -101,21 +111,21 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
         sig[2] += kt;
         if (a.sigma) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a.sigma[c * V + v] = sig[c];
+            for (int c = 0; c < 6; ++c) a.sigma[c * cs + v] = sig[c];
         }
         if (a.eps_p_new) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a.eps_p_new[c * V + v] = ep[c];
+            for (int c = 0; c < 6; ++c) a.eps_p_new[c * cs + v] = ep[c];
         }
         if (a.epbar_new) a.epbar_new[v] = eb + dg;
         if (tg) {
             tg[v] = (TT)K;
-            tg[V + v] = (TT)g2;
-            tg[2 * V + v] = (TT)w[0];
-            tg[3 * V + v] = (TT)w[1];
-            tg[4 * V + v] = (TT)w[3];
-            tg[5 * V + v] = (TT)w[4];
-            tg[6 * V + v] = (TT)w[5];
+            tg[cs + v] = (TT)g2;
+            tg[2 * cs + v] = (TT)w[0];
+            tg[3 * cs + v] = (TT)w[1];
+            tg[4 * cs + v] = (TT)w[3];
+            tg[5 * cs + v] = (TT)w[4];
+            tg[6 * cs + v] = (TT)w[5];
         }
         acc[0] += frob<double>(sig, sig);
 #pragma unroll
@@ -136,6 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
 
 struct VecArgs {
     long long V;
+    long long cs;      // component stride (a multiple of 32, >= V + 4)
     void* x;
     void* r;
     const void* p;
@@ -150,28 +161,52 @@ struct VecArgs {
 };
 
 // x += alpha p; r -= alpha q; rr = <r, r>; then beta, stopping test.
+// 16-byte vectors over the padded components; lanes in the padding are
+// updated too (harmless) but left out of <r, r>.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
     const int f = blockIdx.z;
     CGState* cg = a.cg + f;
     if (cg->done) return;
-    const long long V = a.V;
+    constexpr int VW = 16 / (int)sizeof(T);
+    using VT = typename Vec16<T>::type;
+    const long long V = a.V, cs = a.cs;
+    const long long nv = cs / VW;
     const T alpha = (T)cg->alpha;
-    T* x = (T*)a.x + f * a.fstride;
-    T* r = (T*)a.r + f * a.fstride;
-    const T* p = (const T*)a.p + f * a.fstride;
-    const T* q = (const T*)a.q + f * a.fstride;
+    VT* x = (VT*)((T*)a.x + f * a.fstride);
+    VT* r = (VT*)((T*)a.r + f * a.fstride);
+    const VT* p = (const VT*)((const T*)a.p + f * a.fstride);
+    const VT* q = (const VT*)((const T*)a.q + f * a.fstride);
     T acc = T(0);
-    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
-         v += (long long)gridDim.x * kThreads) {
-        T rv[6];
+    for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < nv;
+         j += (long long)gridDim.x * kThreads) {
+        T rv[6][VW];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            x[c * V + v] += alpha * p[c * V + v];
-            rv[c] = r[c * V + v] - alpha * q[c * V + v];
-            r[c * V + v] = rv[c];
+            VT xv = x[c * nv + j];
+            const VT pv = p[c * nv + j];
+            VT rr = r[c * nv + j];
+            const VT qv = q[c * nv + j];
+            T* xe = reinterpret_cast<T*>(&xv);
+            T* re = reinterpret_cast<T*>(&rr);
+            const T* pe = reinterpret_cast<const T*>(&pv);
+            const T* qe = reinterpret_cast<const T*>(&qv);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                xe[e] += alpha * pe[e];
+                re[e] -= alpha * qe[e];
+                rv[c][e] = re[e];
+            }
+            x[c * nv + j] = xv;
+            r[c * nv + j] = rr;
         }
-        acc += frob<T>(rv, rv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            if (j * VW + e < V) {
+                const T re6[6] = {rv[0][e], rv[1][e], rv[2][e], rv[3][e], rv[4][e], rv[5][e]};
+                acc += frob<T>(re6, re6);
+            }
+        }
     }
     double part[1] = {block_sum((double)acc)};
     double* partials = a.partials + (size_t)f * gridDim.x;
@@ -205,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
 // eps* += x (Algorithm 1, iterative update); nd->de2 = ||x||^2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
-    const long long V = a.V;
+    const long long V = a.V, cs = a.cs;
     const T* x = (const T*)a.x;
     double acc = 0.0;
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
@@ -213,8 +248,8 @@ __global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
         double d[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            d[c] = (double)x[c * V + v];
-            a.eps[c * V + v] += d[c];
+            d[c] = (double)x[c * cs + v];
+            a.eps[c * cs + v] += d[c];
         }
         acc += frob<double>(d, d);
     }
@@ -226,11 +261,11 @@ __global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
 }
 
 template <typename T>
-__device__ __forceinline__ void tangent_apply_v(const T* __restrict__ tg, long long v, long long V,
+__device__ __forceinline__ void tangent_apply_v(const T* __restrict__ tg, long long v, long long cs,
                                                 const double (&p)[6], double (&s)[6]) {
-    const double K = tg[v], g2 = tg[V + v];
-    const double w0 = tg[2 * V + v], w1 = tg[3 * V + v], w3 = tg[4 * V + v], w4 = tg[5 * V + v],
-                 w5 = tg[6 * V + v];
+    const double K = tg[v], g2 = tg[cs + v];
+    const double w0 = tg[2 * cs + v], w1 = tg[3 * cs + v], w3 = tg[4 * cs + v], w4 = tg[5 * cs + v],
+                 w5 = tg[6 * cs + v];
     const double w2 = -(w0 + w1);
     const double tr = p[0] + p[1] + p[2], m = tr / 3.0;
     const double wp = w0 * p[0] + w1 * p[1] + w2 * p[2] + 2.0 * (w3 * p[3] + w4 * p[4] + w5 * p[5]);
@@ -254,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_floor(VecArgs a) {
         for (int j = 0; j < 6; ++j) {
             double e[6] = {0, 0, 0, 0, 0, 0}, s[6];
             e[j] = 1.0;
-            tangent_apply_v<T>(tg, v, V, e, s);
+            tangent_apply_v<T>(tg, v, a.cs, e, s);
             acc[j] += frob<double>(s, s);
         }
     }
@@ -283,8 +318,8 @@ __global__ void __launch_bounds__(kThreads) k_tangent_average(VecArgs a) {
         for (int j = 0; j < 6; ++j) {
             double e[6], s[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) e[c] = (double)x[j * a.fstride + c * V + v] + (c == j ? 1.0 : 0.0);
-            tangent_apply_v<T>(tg, v, V, e, s);
+            for (int c = 0; c < 6; ++c) e[c] = (double)x[j * a.fstride + c * a.cs + v] + (c == j ? 1.0 : 0.0);
+            tangent_apply_v<T>(tg, v, a.cs, e, s);
 #pragma unroll
             for (int i = 0; i < 6; ++i) acc[i * 6 + j] += s[i];
         }
