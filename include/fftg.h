@@ -185,6 +185,37 @@ int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps_d
 int fftg_op_matvec(fftg_handle* h, int precision, const void* p_dev, void* q_dev,
                    double* pq);
 
+/* ---------------------------------------------------------------- no allocation
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory. A host code that has reserved all of its
+ * device memory up front (an FE^2 macro solver with its own pool, calling
+ * the material law from inside its assembly loop) cannot have the library
+ * call cudaMalloc: the call fails while the pool holds the memory, or it
+ * stalls the whole device. This call needs no handle and no workspace.
+ *
+ * It evaluates the J2 update of Section 4.2 at E + eps against the history
+ * (eps_p, epbar), writes sigma [6][N^3] (and, where the pointers are not
+ * NULL, the updated history and the compact tangent [7][N^3] in FP32
+ * (FFTG_MIXED) or FP64 (FFTG_FP64)), and returns the homogenised stress
+ * mean(sigma) in sigma_mean[6] (host). Every field is a caller device buffer
+ * in the unpadded layout [6][N^3] ([N^3] for epbar and phase).
+ *
+ * Its scratch (block partial sums, the reduction ticket, the material table)
+ * is one fixed array of about 240 KB compiled into the library, held by every
+ * GPU that loads it until the process exits. Limits: N <= 243, nphase <= 256;
+ * larger values return FFTG_EINVAL. The first call on a device looks up the
+ * array's device address (once per device, with that device current): make
+ * that first call before any stream capture. All calls share the array and
+ * it keeps the last call's contents, so calls that overlap on the GPU (two
+ * streams, or two host threads) race: serialise them. The call synchronises
+ * `stream` (NULL = legacy default stream) to return sigma_mean. */
+int fftg_constitutive_noalloc(int N, const double E[6], const double* eps_dev,
+                              const double* eps_p_dev, const double* epbar_dev,
+                              const uint8_t* phase_dev, int nphase, const fftg_phase* mats,
+                              int tangent_precision, void* tangent_dev, double* sigma_dev,
+                              double* eps_p_new_dev, double* epbar_new_dev,
+                              double sigma_mean[6], void* stream);
+
 /* ---------------------------------------------------------------- profiling
  * Per-kernel timing of a handle's own launches with CUDA events recorded in
  * its stream around every launch (off by default; a few microseconds per

@@ -94,6 +94,10 @@ SIGNATURES = {
     "fftg_profile_reset": (C.c_int, [C.c_void_p]),
     "fftg_profile_read": (C.c_int, [C.c_void_p, C.c_int, _D6, C.POINTER(C.c_longlong)]),
     "fftg_launch_count": (C.c_longlong, [C.c_void_p]),
+    "fftg_constitutive_noalloc": (C.c_int, [C.c_int, _D6, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_int, C.POINTER(fftg_phase), C.c_int,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _D6,
+                                            C.c_void_p]),
 }
 
 _lib = None
