@@ -125,7 +125,8 @@ int fftg_workspace_size(int N, const fftg_options* opt, size_t* bytes);
 int fftg_create(fftg_handle** h, int N, const uint8_t* phase, int nphase,
                 const fftg_phase* mats, const fftg_options* opt);
 
-/* One load increment (Algorithm 1, one pass of the increment loop):
+/* One load increment (Algorithm 1, one pass of the increment loop) of a
+ * single-cell handle (FFTG_EINVAL for a batch):
  * E <- E + dE, Newton iterations on G sigma(E + eps*) = 0 starting from the
  * previous eps* (Alg. 1 "initial guess for the next increment"), each
  * solving G C d eps* = -G sigma (Eq. linear_system) by CG to the relative
@@ -137,8 +138,28 @@ int fftg_step(fftg_handle* h, const double dE[6], double tol_newton,
               double tol_cg, double sigma_out[6], int* newton_iters,
               int* cg_iters);
 
-/* Diagnostics of the last fftg_step. */
+/* Diagnostics of the last increment of the selected cell. */
 int fftg_last_stats(fftg_handle* h, fftg_stats* out);
+
+/* ---------------------------------------------------------------- batches
+ * A handle may hold ncells cells of the same grid (own microstructure, own
+ * state, own Newton and CG iteration). Every kernel launch of the path then
+ * covers all of them; a cell that has converged skips the work of later
+ * launches. The single-cell calls (fftg_step excepted) act on the cell
+ * chosen by fftg_select_cell (default 0). Not in the paper: the batching
+ * is how many RVE problems (FE^2 Gauss points) share the GPU.
+ * phase is [ncells][N][N][N]. */
+int fftg_workspace_size_batch(int N, int ncells, const fftg_options* opt, size_t* bytes);
+int fftg_create_batch(fftg_handle** h, int N, int ncells, const uint8_t* phase, int nphase,
+                      const fftg_phase* mats, const fftg_options* opt);
+int fftg_batch_size(const fftg_handle* h);
+int fftg_select_cell(fftg_handle* h, int cell);
+/* One load increment for every cell: dE [ncells][6]; outputs
+ * sigma_out [ncells][6], newton_iters / cg_iters [ncells] (may be NULL),
+ * status [ncells] (0 or FFTG_E*; a failed cell is not committed, the others
+ * are). Returns 0 or the first cell's error. */
+int fftg_batch_step(fftg_handle* h, const double* dE, double tol_newton, double tol_cg,
+                    double* sigma_out, int* newton_iters, int* cg_iters, int* status);
 
 /* 6x6 macroscopic algorithmic tangent dSigma/dE at the last converged
  * increment (not in the paper; the quantity an FE^2 macro solver needs).
@@ -184,6 +205,45 @@ int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps_d
  * <p, q> (Frobenius, summed over voxels) to *pq when pq is not NULL. */
 int fftg_op_matvec(fftg_handle* h, int precision, const void* p_dev, void* q_dev,
                    double* pq);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of RVE increments (not in the paper; the FE^2 use of
+ * Section 1: a macro solver issues one strain increment per Gauss point).
+ * A server holds `slots` cells of one grid size (choose slots from the HBM
+ * budget: fftg_workspace_size_batch(N, slots) bytes), one stream and one
+ * worker thread. fftg_server_submit queues (request, session, dE); a new
+ * session must pass its microstructure (N^3 bytes, copied) and starts from
+ * the zero state. The worker admits queued requests into free cells between
+ * Newton iterations, so new work joins the batch already on the GPU; when
+ * every cell is taken it evicts the least recently used idle session to
+ * host memory (its committed state) and restores it on its next request.
+ * Requests of one session run in submission order. A cell's result does
+ * not depend on what shares its launches. */
+typedef struct fftg_server fftg_server;
+typedef struct {
+    long long request_id;
+    long long session_id;
+    int       status;         /* 0 or FFTG_E*; a failed increment is not committed */
+    int       newton_iters;
+    int       cg_iters;
+    double    sigma[6];       /* homogenised stress after the increment */
+    double    t_submit;       /* seconds on fftg_server_clock() */
+    double    t_start;        /* admitted into a cell */
+    double    t_done;
+} fftg_result;
+
+double fftg_server_clock(void);
+int fftg_server_start(fftg_server** s, int N, int slots, int nphase, const fftg_phase* mats,
+                      const fftg_options* opt, double tol_newton, double tol_cg);
+int fftg_server_submit(fftg_server* s, long long request_id, long long session_id,
+                       const uint8_t* phase, const double dE[6]);
+/* Completed requests (up to max) into out; waits up to wait_s seconds when
+ * none is ready. Returns the worker's error code (0 while healthy). */
+int fftg_server_poll(fftg_server* s, fftg_result* out, int max, int* n, double wait_s);
+int fftg_server_info(fftg_server* s, long long* completed, long long* evictions,
+                     long long* restores, int* max_concurrent, double* mean_batch);
+/* Drains the queue, stops the worker and frees everything. */
+int fftg_server_stop(fftg_server* s);
 
 /* ---------------------------------------------------------------- no allocation
  * The paper has no counterpart to this entry point; it serves callers that

@@ -68,12 +68,15 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                                           os.path.join(BUILD, "api.o")])
     units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "noalloc.cu"), "-o",
                                           os.path.join(BUILD, "noalloc.o")])
+    units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "server.cu"), "-o",
+                                          os.path.join(BUILD, "server.o")])
     logs = []
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         for out in ex.map(_run, units):
             logs.append(out)
     objs = ([os.path.join(BUILD, f"passes_{n}.o") for n in GRIDS]
-            + [os.path.join(BUILD, "api.o"), os.path.join(BUILD, "noalloc.o")])
+            + [os.path.join(BUILD, "api.o"), os.path.join(BUILD, "noalloc.o"),
+               os.path.join(BUILD, "server.o")])
     tmp = LIB + ".tmp"
     _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
     os.replace(tmp, LIB)

@@ -1,7 +1,10 @@
 // C-ABI of the fftg library: handle lifetime, the Newton-CG driver of
-// Algorithm 1 and the operator-level entry points. Everything numerical runs
-// in the kernels of passes.cuh and pointwise.cuh; the host only sequences
-// launches and reads a few scalars per Newton iteration.
+// Algorithm 1 over a batch of cells, and the operator-level entry points.
+// Everything numerical runs in the kernels of passes.cuh and pointwise.cuh;
+// the host only sequences launches and reads a few scalars per Newton
+// iteration. A handle holds B >= 1 cells of the same grid: every launch
+// covers all of them, each cell with its own CG and Newton state, and an
+// active mask lets cells join and leave between Newton iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,6 +16,7 @@
 #include <vector>
 
 #include "../../include/fftg.h"
+#include "driver.h"
 #include "passes.cuh"
 #include "pointwise.cuh"
 
@@ -73,6 +77,15 @@ int row_blocks(int N, bool fp64) {
 
 using namespace fftg;
 
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            h->last_cuda = e_;                     \
+            return FFTG_ECUDA;                     \
+        }                                          \
+    } while (0)
+
 namespace {
 enum : int {
     KK_CONSTITUTIVE_F32 = PK_COUNT, KK_CONSTITUTIVE_F64, KK_CG_UPDATE_F32, KK_CG_UPDATE_F64,
@@ -96,16 +109,11 @@ struct Prof {
     double ms[KK_COUNT] = {};
     long long cnt[KK_COUNT] = {};
 };
-}  // namespace
 
-#define CK(call)                                   \
-    do {                                           \
-        cudaError_t e_ = (call);                   \
-        if (e_ != cudaSuccess) {                   \
-            h->last_cuda = e_;                     \
-            return FFTG_ECUDA;                     \
-        }                                          \
-    } while (0)
+// Iterations without a new minimum of <r, r> after which an FP32 inner
+// solve is considered stagnated.
+constexpr int kStagWindow = 25;
+}  // namespace
 
 struct fftg_handle {
     int N = 0;
@@ -114,6 +122,9 @@ struct fftg_handle {
     int H = 0;
     int mixed = 1;
     int nrhs = 6;
+    int B = 1;                   // cells
+    int nf = 6;                  // CG fields held: max(B, nrhs)
+    int sel = 0;                 // cell addressed by the single-cell calls
     fftg_options opt{};
     cudaStream_t stream = nullptr;
     cudaError_t last_cuda = cudaSuccess;
@@ -121,17 +132,18 @@ struct fftg_handle {
     char* ws = nullptr;
     size_t ws_bytes = 0;
 
-    uint8_t* phase = nullptr;
+    uint8_t* phase = nullptr;    // [B][cs]
     double* mats = nullptr;
     int nphase = 0;
-    double* eps_star = nullptr;  // committed
-    double* eps_work = nullptr;  // working copy during an increment
-    double* eps_p[2] = {nullptr, nullptr};
-    double* epbar[2] = {nullptr, nullptr};
-    int hist = 0;                // index of the committed history
-    double* sigma = nullptr;
-    void* tangent = nullptr;     // [7][V] inner precision
-    void* x = nullptr;
+    double* eps_star = nullptr;  // [B][6][cs] committed
+    double* eps_work = nullptr;  // [B][6][cs] trial during an increment
+    double* eps_p = nullptr;     // [B][6][cs] committed
+    double* eps_p_tr = nullptr;  // [B][6][cs] trial
+    double* epbar = nullptr;     // [B][cs] committed
+    double* epbar_tr = nullptr;  // [B][cs] trial
+    double* sigma = nullptr;     // [B][6][cs]
+    void* tangent = nullptr;     // [B][7][cs] inner precision
+    void* x = nullptr;           // [nf][6][cs] inner precision
     void* r = nullptr;
     void* p = nullptr;
     void* q = nullptr;
@@ -139,17 +151,21 @@ struct fftg_handle {
     void* tw32 = nullptr;
     void* tw64 = nullptr;
     double* partials = nullptr;
-    CGState* cg = nullptr;       // [6]
-    NewtonDev* nd = nullptr;
+    CGState* cg = nullptr;       // [nf]
+    NewtonDev* nd = nullptr;     // [B]
+    double* Edev = nullptr;      // [B][6]
+    int* active = nullptr;       // [B]
     double* out36 = nullptr;
 
     CGState* h_cg = nullptr;     // pinned mirrors
     NewtonDev* h_nd = nullptr;
     double* h_out36 = nullptr;
+    double* h_E = nullptr;
+    int* h_active = nullptr;
 
-    double E[6] = {0, 0, 0, 0, 0, 0};
-    bool have_tangent = false;
-    fftg_stats stats{};
+    std::vector<double> E;           // [B][6] committed
+    std::vector<char> have_tangent;  // [B]
+    std::vector<fftg_stats> stats;   // [B]
     long long launches = 0;
     Prof* prof = nullptr;
 };
@@ -199,12 +215,6 @@ namespace {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-struct Layout {
-    size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p0, off_eps_p1, off_epbar0,
-        off_epbar1, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32, off_tw64,
-        off_partials, off_cg, off_nd, off_out36, total;
-};
-
 // Component stride of every field: N^3 rounded up past N^3 + 4 to a
 // multiple of 32 elements, so each component starts 128-byte aligned and a
 // 16-byte vector that straddles the end of the grid stays in the padding.
@@ -213,15 +223,23 @@ long long comp_stride(int N) {
     return ((V + 4 + 31) / 32) * 32;
 }
 
-Layout make_layout(int N, int mixed, int nrhs) {
-    const size_t V = (size_t)comp_stride(N);
+struct Layout {
+    size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p, off_eps_p_tr, off_epbar,
+        off_epbar_tr, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32,
+        off_tw64, off_partials, off_cg, off_nd, off_E, off_active, off_out36, total;
+};
+
+Layout make_layout(int N, int mixed, int nrhs, int B) {
+    const size_t cs = (size_t)comp_stride(N);
     const size_t H = (size_t)(N + 1) / 2;
     const size_t ts = mixed ? 4 : 8;
-    const size_t nf = (size_t)std::max(1, nrhs);
-    const size_t spec64 = 6 * (size_t)N * N * H * 16;
-    const size_t specT = nf * 6 * (size_t)N * N * H * (2 * ts);
+    const size_t nf = (size_t)std::max(B, std::max(1, nrhs));
+    const size_t spec1 = 6 * (size_t)N * N * H;  // complex elements per field
+    const size_t spec = std::max((size_t)B * spec1 * 16, nf * spec1 * 2 * ts);
     const size_t rb = (size_t)std::max(fftg::row_blocks(N, true), fftg::row_blocks(N, false));
-    const size_t npart = std::max((size_t)kMaxPointwiseBlocks * 36, rb * 2 * 6);
+    const size_t npart = std::max({(size_t)kMaxPointwiseBlocks * 36, rb * 2 * nf,
+                                   (size_t)B * kMaxPointwiseBlocks * 7, nf * 2432});
+    const size_t Bs = (size_t)B;
     Layout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -229,26 +247,28 @@ Layout make_layout(int N, int mixed, int nrhs) {
         o += align256(bytes);
         return at;
     };
-    L.off_phase = take((size_t)N * N * N);
+    L.off_phase = take(Bs * cs);
     L.off_mats = take(256 * 4 * 8);
-    L.off_eps_star = take(6 * V * 8);
-    L.off_eps_work = take(6 * V * 8);
-    L.off_eps_p0 = take(6 * V * 8);
-    L.off_eps_p1 = take(6 * V * 8);
-    L.off_epbar0 = take(V * 8);
-    L.off_epbar1 = take(V * 8);
-    L.off_sigma = take(6 * V * 8);
-    L.off_tangent = take(7 * V * ts);
-    L.off_x = take(nf * 6 * V * ts);
-    L.off_r = take(nf * 6 * V * ts);
-    L.off_p = take(nf * 6 * V * ts);
-    L.off_q = take(nf * 6 * V * ts);
-    L.off_spec = take(std::max(spec64, specT));
+    L.off_eps_star = take(Bs * 6 * cs * 8);
+    L.off_eps_work = take(Bs * 6 * cs * 8);
+    L.off_eps_p = take(Bs * 6 * cs * 8);
+    L.off_eps_p_tr = take(Bs * 6 * cs * 8);
+    L.off_epbar = take(Bs * cs * 8);
+    L.off_epbar_tr = take(Bs * cs * 8);
+    L.off_sigma = take(Bs * 6 * cs * 8);
+    L.off_tangent = take(Bs * 7 * cs * ts);
+    L.off_x = take(nf * 6 * cs * ts);
+    L.off_r = take(nf * 6 * cs * ts);
+    L.off_p = take(nf * 6 * cs * ts);
+    L.off_q = take(nf * 6 * cs * ts);
+    L.off_spec = take(spec);
     L.off_tw32 = take((size_t)N * 8);
     L.off_tw64 = take((size_t)N * 16);
     L.off_partials = take(npart * 8);
-    L.off_cg = take(6 * sizeof(CGState));
-    L.off_nd = take(sizeof(NewtonDev));
+    L.off_cg = take(nf * sizeof(CGState));
+    L.off_nd = take(Bs * sizeof(NewtonDev));
+    L.off_E = take(Bs * 6 * 8);
+    L.off_active = take(Bs * 4);
     L.off_out36 = take(36 * 8);
     L.total = o;
     return L;
@@ -283,43 +303,6 @@ void twiddles(int N, double* tw64, float* tw32) {
 }  // namespace
 
 // ---------------------------------------------------------------- internals
-static int sync_read(fftg_handle* h, bool cg_all, bool nd) {
-    if (cg_all) CK(cudaMemcpyAsync(h->h_cg, h->cg, 6 * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
-    if (nd) CK(cudaMemcpyAsync(h->h_nd, h->nd, sizeof(NewtonDev), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    return FFTG_OK;
-}
-
-static int launch_constitutive(fftg_handle* h, const double E[6], const double* eps, double* sigma,
-                               bool write_history, CGState* cg, bool write_tangent = true) {
-    ConstArgs a{};
-    a.V = h->V;
-    a.cs = h->cs;
-    for (int c = 0; c < 6; ++c) a.E[c] = E[c];
-    a.eps = eps;
-    a.eps_p = h->eps_p[h->hist];
-    a.epbar = h->epbar[h->hist];
-    a.phase = h->phase;
-    a.mats = h->mats;
-    a.sigma = sigma;
-    a.eps_p_new = write_history ? h->eps_p[1 - h->hist] : nullptr;
-    a.epbar_new = write_history ? h->epbar[1 - h->hist] : nullptr;
-    a.tangent = write_tangent ? h->tangent : nullptr;
-    a.partials = h->partials;
-    a.nd = h->nd;
-    a.cg = cg;
-    a.tie = 1e-12;
-    const int nb = pointwise_blocks(h->V);
-    const int slot = prof_begin(h, h->mixed ? KK_CONSTITUTIVE_F32 : KK_CONSTITUTIVE_F64);
-    if (h->mixed)
-        k_constitutive<float><<<nb, kThreads, 0, h->stream>>>(a);
-    else
-        k_constitutive<double><<<nb, kThreads, 0, h->stream>>>(a);
-    prof_end(h, slot);
-    CK(cudaGetLastError());
-    return FFTG_OK;
-}
-
 static PassArgs base_args(fftg_handle* h, bool fp64) {
     PassArgs a{};
     a.tw = fp64 ? h->tw64 : h->tw32;
@@ -341,48 +324,97 @@ static cudaError_t copy_field(fftg_handle* h, void* dst, bool dst_padded, const 
     return cudaMemcpy2DAsync(dst, dp, src, sp, w, ncomp, kind, h->stream);
 }
 
+static inline double* cell_field(double* base, const fftg_handle* h, int c) {
+    return base + (size_t)c * 6 * h->cs;
+}
+
+// Constitutive update of `ncells` cells starting at cell0 at E (Edev, one
+// 6-vector per cell) + eps against the committed history; mask_dev (may be
+// null) skips cells.
+static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, int cell0,
+                               const double* eps, double* sigma, bool write_history, CGState* cg,
+                               bool write_tangent = true) {
+    ConstArgs a{};
+    a.V = h->V;
+    a.cs = h->cs;
+    a.Edev = h->Edev + 6 * cell0;
+    a.eps = eps + (size_t)cell0 * 6 * h->cs;
+    a.eps_p = h->eps_p + (size_t)cell0 * 6 * h->cs;
+    a.epbar = h->epbar + (size_t)cell0 * h->cs;
+    a.phase = h->phase + (size_t)cell0 * h->cs;
+    a.mats = h->mats;
+    a.sigma = sigma ? sigma + (size_t)cell0 * 6 * h->cs : nullptr;
+    a.eps_p_new = write_history ? h->eps_p_tr + (size_t)cell0 * 6 * h->cs : nullptr;
+    a.epbar_new = write_history ? h->epbar_tr + (size_t)cell0 * h->cs : nullptr;
+    a.tangent = write_tangent ? (char*)h->tangent + (size_t)cell0 * 7 * h->cs * (h->mixed ? 4 : 8)
+                              : nullptr;
+    a.partials = h->partials;
+    a.nd = h->nd + cell0;
+    a.cg = cg ? cg + cell0 : nullptr;
+    a.tie = 1e-12;
+    a.active = mask_dev ? mask_dev + cell0 : nullptr;
+    a.cell_fields = 6 * h->cs;
+    a.cell_scalar = h->cs;
+    a.cell_tangent = 7 * h->cs;
+    const dim3 g(pointwise_blocks(h->V), ncells);
+    const int slot = prof_begin(h, h->mixed ? KK_CONSTITUTIVE_F32 : KK_CONSTITUTIVE_F64);
+    if (h->mixed)
+        k_constitutive<float><<<g, kThreads, 0, h->stream>>>(a);
+    else
+        k_constitutive<double><<<g, kThreads, 0, h->stream>>>(a);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    return FFTG_OK;
+}
+
 // Forward-project-inverse core on the spectrum buffer (P2, P3, P4).
-static int run_p234(fftg_handle* h, bool fp64, double scale, CGState* cg, int nf) {
+static int run_p234(fftg_handle* h, bool fp64, double scale, CGState* cg, int nf, const int* mask) {
     PassArgs a = base_args(h, fp64);
     a.out = h->spec;
     a.cg = cg;
     a.scale = scale;
+    a.active = mask;
     CK(pass(h, fp64 ? PK_P2_F64 : PK_P2_F32, a, nf));
     CK(pass(h, fp64 ? PK_P3_F64 : PK_P3_F32, a, nf));
     CK(pass(h, fp64 ? PK_P4_F64 : PK_P4_F32, a, nf));
     return FFTG_OK;
 }
 
-// r = -G sigma (FP64 FFT), rounded to the inner precision; x = 0.
+// r = -G sigma (FP64 FFT) for the cells in the active mask, rounded to the
+// inner precision; x = 0.
 static int launch_residual(fftg_handle* h) {
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     PassArgs a = base_args(h, true);
     a.in = h->sigma;
     a.out = h->spec;
-    CK(pass(h, PK_P1_PLAIN_F64, a, 1));
-    int rc = run_p234(h, true, -invN3, nullptr, 1);
+    a.active = h->active;
+    CK(pass(h, PK_P1_PLAIN_F64, a, h->B));
+    int rc = run_p234(h, true, -invN3, nullptr, h->B, h->active);
     if (rc) return rc;
     PassArgs b = base_args(h, true);
     b.in = h->spec;
     b.out = h->r;
     b.cg = h->cg;
-    CK(pass(h, h->mixed ? PK_P5_RHS_F64_TO_F32 : PK_P5_RHS_F64_TO_F64, b, 1));
-    CK(cudaMemsetAsync(h->x, 0, 6 * h->cs * (h->mixed ? 4 : 8), h->stream));
+    b.active = h->active;
+    CK(pass(h, h->mixed ? PK_P5_RHS_F64_TO_F32 : PK_P5_RHS_F64_TO_F64, b, h->B));
+    CK(cudaMemsetAsync(h->x, 0, (size_t)h->B * 6 * h->cs * (h->mixed ? 4 : 8), h->stream));
     return FFTG_OK;
 }
 
 // One CG iteration on nf fields: the fused matvec passes and the update.
-static int launch_cg_iteration(fftg_handle* h, int nf) {
+// `tangent`/`tstride`: per-field tangents (batched cells) or one shared.
+static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long long tstride) {
     const bool f64 = !h->mixed;
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     PassArgs a = base_args(h, f64);
     a.aux = h->r;
     a.aux2 = h->p;
-    a.tangent = h->tangent;
+    a.tangent = tangent;
+    a.tstride = tstride;
     a.out = h->spec;
     a.cg = h->cg;
     CK(pass(h, f64 ? PK_P1_CG_F64 : PK_P1_CG_F32, a, nf));
-    int rc = run_p234(h, f64, invN3, h->cg, nf);
+    int rc = run_p234(h, f64, invN3, h->cg, nf, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
@@ -414,8 +446,8 @@ static int launch_cg_iteration(fftg_handle* h, int nf) {
 // Runs CG iterations until every one of the nf solves is done. Iterations
 // are enqueued in chunks; kernels of a finished solve return at entry, so a
 // chunk may overrun the last iteration without effect.
-static int run_cg(fftg_handle* h, int nf) {
-    CK(cudaMemcpyAsync(h->h_cg, h->cg, 6 * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+static int run_cg(fftg_handle* h, int nf, const void* tangent, long long tstride) {
+    CK(cudaMemcpyAsync(h->h_cg, h->cg, nf * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     int chunk = 2;
     int launched = 0;
@@ -426,23 +458,19 @@ static int run_cg(fftg_handle* h, int nf) {
         if (all) break;
         if (launched > cap) return FFTG_ENOCONV_CG;  // defensive: should not happen
         for (int k = 0; k < chunk; ++k) {
-            int rc = launch_cg_iteration(h, nf);
+            int rc = launch_cg_iteration(h, nf, tangent, tstride);
             if (rc) return rc;
         }
         launched += chunk;
         chunk = std::min(chunk * 2, 16);
-        CK(cudaMemcpyAsync(h->h_cg, h->cg, 6 * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(h->h_cg, h->cg, nf * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
     }
     return FFTG_OK;
 }
 
-// Iterations without a new minimum of <r, r> after which an FP32 inner
-// solve is considered stagnated.
-constexpr int kStagWindow = 25;
-
-static void set_cg_params(fftg_handle* h, int nf, double tol) {
-    for (int f = 0; f < 6; ++f) {
+static void set_cg_params(fftg_handle* h, int nf, double tol, const int* run) {
+    for (int f = 0; f < h->nf; ++f) {
         CGState& c = h->h_cg[f];
         std::memset(&c, 0, sizeof(CGState));
         c.tol2 = tol * tol;
@@ -450,8 +478,237 @@ static void set_cg_params(fftg_handle* h, int nf, double tol) {
         c.fixed_it = h->opt.fixed_cg;
         // the FP32 inner solve stops when it stagnates (FP64 Newton refines)
         c.stag_window = (h->mixed && h->opt.fixed_cg <= 0) ? kStagWindow : 0;
-        c.done = f < nf ? CG_RUNNING : CG_CONVERGED;
+        const bool on = f < nf && (!run || run[f]);
+        c.done = on ? CG_RUNNING : CG_CONVERGED;
     }
+}
+
+// ---------------------------------------------------------------- Newton rounds
+namespace fftg_detail {
+
+int newton_round(fftg_handle* h, const int* run, double tol_inner, RoundOut* out) {
+    const int B = h->B;
+    for (int b = 0; b < B; ++b) h->h_active[b] = run[b];
+    CK(cudaMemcpyAsync(h->active, h->h_active, B * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    set_cg_params(h, B, tol_inner, run);
+    CK(cudaMemcpyAsync(h->cg, h->h_cg, h->nf * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+    int rc = launch_constitutive(h, h->active, B, 0, h->eps_work, h->sigma, false, h->cg);
+    if (rc) return rc;
+    rc = launch_residual(h);
+    if (rc) return rc;
+    rc = run_cg(h, B, h->tangent, 7 * h->cs);
+    if (rc) return rc;
+    VecArgs u{};
+    u.V = h->V;
+    u.cs = h->cs;
+    u.x = h->x;
+    u.eps = h->eps_work;
+    u.nd = h->nd;
+    u.partials = h->partials;
+    u.active = h->active;
+    u.fstride = 6 * h->cs;
+    u.cell_fields = 6 * h->cs;
+    const dim3 g(pointwise_blocks(h->V), B);
+    const int slot = prof_begin(h, h->mixed ? KK_NEWTON_UPDATE_F32 : KK_NEWTON_UPDATE_F64);
+    if (h->mixed)
+        k_newton_update<float><<<g, kThreads, 0, h->stream>>>(u);
+    else
+        k_newton_update<double><<<g, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_cg, h->cg, B * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->h_nd, h->nd, B * sizeof(NewtonDev), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < B; ++b) {
+        if (!run[b]) continue;
+        const CGState& c = h->h_cg[b];
+        out[b].cg_it = c.it;
+        out[b].cg_done = c.done;
+        out[b].de2 = h->h_nd[b].de2;
+        out[b].gs2 = c.gs2;
+        out[b].sig2 = h->h_nd[b].sig2;
+        out[b].relres = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
+    }
+    return FFTG_OK;
+}
+
+int set_trial_strain(fftg_handle* h, int cell, const double Et[6], bool copy_eps) {
+    std::memcpy(h->h_E + 6 * cell, Et, 6 * sizeof(double));
+    CK(cudaMemcpyAsync(h->Edev + 6 * cell, h->h_E + 6 * cell, 6 * sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    if (copy_eps)
+        CK(cudaMemcpyAsync(cell_field(h->eps_work, h, cell), cell_field(h->eps_star, h, cell),
+                           6 * h->cs * 8, cudaMemcpyDeviceToDevice, h->stream));
+    return FFTG_OK;
+}
+
+// Final constitutive call of the cells in `fin` (history out), their
+// homogenised stress, and the commit of their trial state.
+int finish_cells(fftg_handle* h, const int* fin, double* sigma_out) {
+    const int B = h->B;
+    for (int b = 0; b < B; ++b) h->h_active[b] = fin[b];
+    CK(cudaMemcpyAsync(h->active, h->h_active, B * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    int rc = launch_constitutive(h, h->active, B, 0, h->eps_work, h->sigma, true, nullptr);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->h_nd, h->nd, B * sizeof(NewtonDev), cudaMemcpyDeviceToHost, h->stream));
+    int all = 1;
+    for (int b = 0; b < B; ++b) all &= fin[b];
+    if (all) {
+        CK(cudaMemcpyAsync(h->eps_star, h->eps_work, (size_t)B * 6 * h->cs * 8, cudaMemcpyDeviceToDevice,
+                           h->stream));
+        CK(cudaMemcpyAsync(h->eps_p, h->eps_p_tr, (size_t)B * 6 * h->cs * 8, cudaMemcpyDeviceToDevice,
+                           h->stream));
+        CK(cudaMemcpyAsync(h->epbar, h->epbar_tr, (size_t)B * h->cs * 8, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    } else {
+        for (int b = 0; b < B; ++b) {
+            if (!fin[b]) continue;
+            CK(cudaMemcpyAsync(cell_field(h->eps_star, h, b), cell_field(h->eps_work, h, b), 6 * h->cs * 8,
+                               cudaMemcpyDeviceToDevice, h->stream));
+            CK(cudaMemcpyAsync(cell_field(h->eps_p, h, b), cell_field(h->eps_p_tr, h, b), 6 * h->cs * 8,
+                               cudaMemcpyDeviceToDevice, h->stream));
+            CK(cudaMemcpyAsync(h->epbar + (size_t)b * h->cs, h->epbar_tr + (size_t)b * h->cs, h->cs * 8,
+                               cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < B; ++b) {
+        if (!fin[b]) continue;
+        for (int c = 0; c < 6; ++c) {
+            sigma_out[6 * b + c] = h->h_nd[b].sum[c] / (double)h->V;
+            h->E[6 * b + c] = h->h_E[6 * b + c];
+        }
+        h->have_tangent[b] = 1;
+    }
+    return FFTG_OK;
+}
+
+int cells(const fftg_handle* h) { return h->B; }
+int grid_n(const fftg_handle* h) { return h->N; }
+bool is_mixed(const fftg_handle* h) { return h->mixed != 0; }
+const fftg_options& options(const fftg_handle* h) { return h->opt; }
+const double* committed_E(const fftg_handle* h, int cell) { return h->E.data() + 6 * cell; }
+long long voxels(const fftg_handle* h) { return h->V; }
+
+int upload_cell(fftg_handle* h, int cell, const uint8_t* phase, const double* state) {
+    if (phase)
+        CK(cudaMemcpyAsync(h->phase + (size_t)cell * h->cs, phase, h->V, cudaMemcpyHostToDevice, h->stream));
+    if (state) {
+        const double* d = state;
+        CK(copy_field(h, cell_field(h->eps_star, h, cell), true, d + 6, false, 8, cudaMemcpyHostToDevice));
+        CK(copy_field(h, cell_field(h->eps_p, h, cell), true, d + 6 + 6 * h->V, false, 8,
+                      cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(h->epbar + (size_t)cell * h->cs, d + 6 + 12 * h->V, h->V * 8,
+                           cudaMemcpyHostToDevice, h->stream));
+        std::memcpy(h->E.data() + 6 * cell, d, 6 * sizeof(double));
+    } else {
+        CK(cudaMemsetAsync(cell_field(h->eps_star, h, cell), 0, 6 * h->cs * 8, h->stream));
+        CK(cudaMemsetAsync(cell_field(h->eps_p, h, cell), 0, 6 * h->cs * 8, h->stream));
+        CK(cudaMemsetAsync(h->epbar + (size_t)cell * h->cs, 0, h->cs * 8, h->stream));
+        std::fill(h->E.begin() + 6 * cell, h->E.begin() + 6 * cell + 6, 0.0);
+    }
+    h->have_tangent[cell] = 0;
+    CK(cudaStreamSynchronize(h->stream));
+    return FFTG_OK;
+}
+
+int download_cell(fftg_handle* h, int cell, double* state) {
+    double* d = state;
+    std::memcpy(d, h->E.data() + 6 * cell, 6 * sizeof(double));
+    CK(copy_field(h, d + 6, false, cell_field(h->eps_star, h, cell), true, 8, cudaMemcpyDeviceToHost));
+    CK(copy_field(h, d + 6 + 6 * h->V, false, cell_field(h->eps_p, h, cell), true, 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(d + 6 + 12 * h->V, h->epbar + (size_t)cell * h->cs, h->V * 8, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FFTG_OK;
+}
+
+// Newton test of one cell after a round (Algorithm 1): returns 0 while the
+// cell keeps iterating, 1 when it has converged, or an FFTG_E* code.
+int newton_decide(fftg_handle* h, int cell, const RoundOut& ro, double normE, double tol_newton, int* it) {
+    fftg_stats& st = h->stats[cell];
+    const double nde = std::sqrt(ro.de2);
+    const double rel = normE > 0 ? nde / normE : (nde == 0 ? 0.0 : INFINITY);
+    const int i = *it;
+    if (i < FFTG_MAX_NEWTON_LOG) {
+        st.cg_per_newton[i] = ro.cg_it;
+        st.newton_norm[i] = rel;
+        st.residual[i] = ro.sig2 > 0 ? std::sqrt(ro.gs2 / ro.sig2) : 0.0;
+        st.cg_relres[i] = ro.relres;
+        st.cg_status[i] = ro.cg_done;
+    }
+    st.cg_iters += ro.cg_it;
+    *it = i + 1;
+    st.newton_iters = *it;
+    if (ro.cg_done == CG_BREAKDOWN || !std::isfinite(rel)) return FFTG_ENAN;
+    if (h->opt.fixed_newton > 0) return *it >= h->opt.fixed_newton ? 1 : 0;
+    if (rel <= tol_newton || nde == 0.0) return 1;
+    if (*it >= h->opt.max_newton) return FFTG_ENOCONV_NEWTON;
+    return 0;
+}
+
+void reset_stats(fftg_handle* h, int cell) {
+    std::memset(&h->stats[cell], 0, sizeof(fftg_stats));
+    h->have_tangent[cell] = 0;
+}
+
+void set_status(fftg_handle* h, int cell, int status) { h->stats[cell].status = status; }
+
+}  // namespace fftg_detail
+
+using namespace fftg_detail;
+
+// One increment for every cell (Algorithm 1, increment loop body), cells in
+// lock step but each with its own Newton test.
+static int batch_step(fftg_handle* h, const double* dE, double tol_newton, double tol_cg, double* sigma_out,
+                      int* newton_iters, int* cg_iters, int* status) {
+    const int B = h->B;
+    const double tol_inner = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
+    std::vector<double> normE(B);
+    std::vector<int> run(B, 1), fin(B, 0), it(B, 0);
+    for (int b = 0; b < B; ++b) {
+        double Et[6];
+        for (int c = 0; c < 6; ++c) Et[c] = h->E[6 * b + c] + dE[6 * b + c];
+        normE[b] = std::sqrt((double)h->V) * frob6(Et);
+        std::memcpy(h->h_E + 6 * b, Et, sizeof(Et));
+        reset_stats(h, b);
+        status[b] = FFTG_OK;
+    }
+    CK(cudaMemcpyAsync(h->Edev, h->h_E, (size_t)B * 6 * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->eps_work, h->eps_star, (size_t)B * 6 * h->cs * 8, cudaMemcpyDeviceToDevice, h->stream));
+    std::vector<RoundOut> ro(B);
+    for (;;) {
+        bool any = false;
+        for (int b = 0; b < B; ++b) any = any || run[b];
+        if (!any) break;
+        int rc = newton_round(h, run.data(), tol_inner, ro.data());
+        if (rc) return rc;
+        for (int b = 0; b < B; ++b) {
+            if (!run[b]) continue;
+            const int d = newton_decide(h, b, ro[b], normE[b], tol_newton, &it[b]);
+            if (d == 1) {
+                run[b] = 0;
+                fin[b] = 1;
+            } else if (d < 0) {
+                status[b] = d;
+                run[b] = 0;
+            }
+        }
+    }
+    bool anyfin = false;
+    for (int b = 0; b < B; ++b) anyfin = anyfin || fin[b];
+    if (anyfin) {
+        int rc = finish_cells(h, fin.data(), sigma_out);
+        if (rc) return rc;
+    }
+    int first = FFTG_OK;
+    for (int b = 0; b < B; ++b) {
+        h->stats[b].status = status[b];
+        if (newton_iters) newton_iters[b] = it[b];
+        if (cg_iters) cg_iters[b] = h->stats[b].cg_iters;
+        if (status[b] != FFTG_OK && first == FFTG_OK) first = status[b];
+    }
+    return first;
 }
 
 // ---------------------------------------------------------------- public API
@@ -467,20 +724,25 @@ void fftg_default_options(fftg_options* o) {
     o->nrhs_tangent = 6;
 }
 
-const char* fftg_version(void) { return "fftg 0.1 (sm_103a)"; }
+const char* fftg_version(void) { return "fftg 0.2 (sm_103a)"; }
 
-int fftg_workspace_size(int N, const fftg_options* opt, size_t* bytes) {
-    if (!bytes || !valid_grid(N)) return FFTG_EINVAL;
+int fftg_workspace_size_batch(int N, int ncells, const fftg_options* opt, size_t* bytes) {
+    if (!bytes || !valid_grid(N) || ncells < 1) return FFTG_EINVAL;
     fftg_options o;
     if (opt) o = *opt; else fftg_default_options(&o);
     if (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) return FFTG_EINVAL;
-    *bytes = make_layout(N, o.precision == FFTG_MIXED, o.nrhs_tangent).total;
+    *bytes = make_layout(N, o.precision == FFTG_MIXED, o.nrhs_tangent, ncells).total;
     return FFTG_OK;
 }
 
-int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, const fftg_phase* mats,
-                const fftg_options* opt) {
-    if (!out || !phase || !mats || nphase < 1 || nphase > 256 || !valid_grid(N)) return FFTG_EINVAL;
+int fftg_workspace_size(int N, const fftg_options* opt, size_t* bytes) {
+    return fftg_workspace_size_batch(N, 1, opt, bytes);
+}
+
+int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase, int nphase,
+                      const fftg_phase* mats, const fftg_options* opt) {
+    if (!out || !phase || !mats || nphase < 1 || nphase > 256 || !valid_grid(N) || ncells < 1)
+        return FFTG_EINVAL;
     *out = nullptr;
     fftg_options o;
     if (opt) o = *opt; else fftg_default_options(&o);
@@ -491,7 +753,7 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
         if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0))
             return FFTG_EINVAL;
     const size_t V = (size_t)N * N * N;
-    for (size_t v = 0; v < V; ++v)
+    for (size_t v = 0; v < V * (size_t)ncells; ++v)
         if (phase[v] >= nphase) return FFTG_EINVAL;
 
     fftg_handle* h = new (std::nothrow) fftg_handle();
@@ -502,10 +764,15 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
     h->H = (N + 1) / 2;
     h->mixed = o.precision == FFTG_MIXED;
     h->nrhs = o.nrhs_tangent;
+    h->B = ncells;
+    h->nf = std::max(ncells, std::max(1, h->nrhs));
     h->opt = o;
     h->stream = (cudaStream_t)o.stream;
     h->nphase = nphase;
-    const Layout L = make_layout(N, h->mixed, h->nrhs);
+    h->E.assign((size_t)6 * ncells, 0.0);
+    h->have_tangent.assign(ncells, 0);
+    h->stats.assign(ncells, fftg_stats{});
+    const Layout L = make_layout(N, h->mixed, h->nrhs, ncells);
     if (o.workspace) {
         if (o.workspace_bytes < L.total || ((uintptr_t)o.workspace & 255u)) {
             delete h;
@@ -526,10 +793,10 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
     h->mats = (double*)(h->ws + L.off_mats);
     h->eps_star = (double*)(h->ws + L.off_eps_star);
     h->eps_work = (double*)(h->ws + L.off_eps_work);
-    h->eps_p[0] = (double*)(h->ws + L.off_eps_p0);
-    h->eps_p[1] = (double*)(h->ws + L.off_eps_p1);
-    h->epbar[0] = (double*)(h->ws + L.off_epbar0);
-    h->epbar[1] = (double*)(h->ws + L.off_epbar1);
+    h->eps_p = (double*)(h->ws + L.off_eps_p);
+    h->eps_p_tr = (double*)(h->ws + L.off_eps_p_tr);
+    h->epbar = (double*)(h->ws + L.off_epbar);
+    h->epbar_tr = (double*)(h->ws + L.off_epbar_tr);
     h->sigma = (double*)(h->ws + L.off_sigma);
     h->tangent = h->ws + L.off_tangent;
     h->x = h->ws + L.off_x;
@@ -542,15 +809,19 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
     h->partials = (double*)(h->ws + L.off_partials);
     h->cg = (CGState*)(h->ws + L.off_cg);
     h->nd = (NewtonDev*)(h->ws + L.off_nd);
+    h->Edev = (double*)(h->ws + L.off_E);
+    h->active = (int*)(h->ws + L.off_active);
     h->out36 = (double*)(h->ws + L.off_out36);
 
     auto fail = [&](int code) {
         fftg_destroy(h);
         return code;
     };
-    if (cudaMallocHost((void**)&h->h_cg, 6 * sizeof(CGState)) != cudaSuccess ||
-        cudaMallocHost((void**)&h->h_nd, sizeof(NewtonDev)) != cudaSuccess ||
-        cudaMallocHost((void**)&h->h_out36, 36 * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&h->h_cg, h->nf * sizeof(CGState)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_nd, ncells * sizeof(NewtonDev)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_out36, 36 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_E, (size_t)ncells * 6 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_active, ncells * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return fail(FFTG_ENOMEM);
     }
@@ -565,22 +836,30 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
         m[4 * i + 3] = mats[i].H;
     }
     cudaStream_t s = h->stream;
-    if (cudaMemcpyAsync(h->phase, phase, V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(h->mats, m.data(), m.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    bool ok = true;
+    for (int b = 0; b < ncells && ok; ++b)
+        ok = cudaMemcpyAsync(h->phase + (size_t)b * h->cs, phase + (size_t)b * V, V, cudaMemcpyHostToDevice,
+                             s) == cudaSuccess;
+    if (!ok || cudaMemcpyAsync(h->mats, m.data(), m.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw64, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw32, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(h->eps_star, 0, 6 * h->cs * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(h->eps_p[0], 0, 6 * h->cs * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(h->epbar[0], 0, V * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(h->cg, 0, 6 * sizeof(CGState), s) != cudaSuccess ||
-        cudaMemsetAsync(h->nd, 0, sizeof(NewtonDev), s) != cudaSuccess ||
+        cudaMemsetAsync(h->eps_star, 0, (size_t)ncells * 6 * h->cs * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->eps_p, 0, (size_t)ncells * 6 * h->cs * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->epbar, 0, (size_t)ncells * h->cs * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->cg, 0, h->nf * sizeof(CGState), s) != cudaSuccess ||
+        cudaMemsetAsync(h->nd, 0, ncells * sizeof(NewtonDev), s) != cudaSuccess ||
+        cudaMemsetAsync(h->Edev, 0, (size_t)ncells * 6 * 8, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         h->last_cuda = cudaGetLastError();
         return fail(FFTG_ECUDA);
     }
-    h->hist = 0;
     *out = h;
     return FFTG_OK;
+}
+
+int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, const fftg_phase* mats,
+                const fftg_options* opt) {
+    return fftg_create_batch(out, N, 1, phase, nphase, mats, opt);
 }
 
 void fftg_destroy(fftg_handle* h) {
@@ -590,6 +869,8 @@ void fftg_destroy(fftg_handle* h) {
     if (h->h_cg) cudaFreeHost(h->h_cg);
     if (h->h_nd) cudaFreeHost(h->h_nd);
     if (h->h_out36) cudaFreeHost(h->h_out36);
+    if (h->h_E) cudaFreeHost(h->h_E);
+    if (h->h_active) cudaFreeHost(h->h_active);
     if (h->prof) {
         for (int i = 0; i < Prof::kRing; ++i) {
             if (h->prof->ev0[i]) cudaEventDestroy(h->prof->ev0[i]);
@@ -598,6 +879,14 @@ void fftg_destroy(fftg_handle* h) {
         delete h->prof;
     }
     delete h;
+}
+
+int fftg_batch_size(const fftg_handle* h) { return h ? h->B : 0; }
+
+int fftg_select_cell(fftg_handle* h, int cell) {
+    if (!h || cell < 0 || cell >= h->B) return FFTG_EINVAL;
+    h->sel = cell;
+    return FFTG_OK;
 }
 
 int fftg_profile_kinds(void) { return KK_COUNT; }
@@ -645,118 +934,45 @@ int fftg_profile_read(fftg_handle* h, int kind, double* total_ms, long long* lau
 
 long long fftg_launch_count(const fftg_handle* h) { return h ? h->launches : 0; }
 
+int fftg_batch_step(fftg_handle* h, const double* dE, double tol_newton, double tol_cg, double* sigma_out,
+                    int* newton_iters, int* cg_iters, int* status) {
+    if (!h || !dE || !sigma_out || !status || !(tol_newton > 0) || !(tol_cg > 0)) return FFTG_EINVAL;
+    for (int k = 0; k < 6 * h->B; ++k)
+        if (!std::isfinite(dE[k])) return FFTG_ENAN;
+    return batch_step(h, dE, tol_newton, tol_cg, sigma_out, newton_iters, cg_iters, status);
+}
+
 int fftg_step(fftg_handle* h, const double dE[6], double tol_newton, double tol_cg, double sigma_out[6],
               int* newton_iters, int* cg_iters) {
     if (!h || !dE || !sigma_out || !(tol_newton > 0) || !(tol_cg > 0)) return FFTG_EINVAL;
+    if (h->B != 1) return FFTG_EINVAL;
     for (int c = 0; c < 6; ++c)
         if (!std::isfinite(dE[c])) return FFTG_ENAN;
-    fftg_stats& st = h->stats;
-    std::memset(&st, 0, sizeof(st));
-    double Et[6];
-    for (int c = 0; c < 6; ++c) Et[c] = h->E[c] + dE[c];
-    const double normE = std::sqrt((double)h->V) * frob6(Et);
-    const double tol_inner = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
-    CK(cudaMemcpyAsync(h->eps_work, h->eps_star, 6 * h->cs * 8, cudaMemcpyDeviceToDevice, h->stream));
-    h->have_tangent = false;
-    int it = 0;
-    bool converged = false;
-    int status = FFTG_OK;
-    for (;;) {
-        set_cg_params(h, 1, tol_inner);
-        CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
-        int rc = launch_constitutive(h, Et, h->eps_work, h->sigma, false, h->cg);
-        if (rc) return rc;
-        rc = launch_residual(h);
-        if (rc) return rc;
-        rc = run_cg(h, 1);
-        if (rc) return rc;
-        VecArgs u{};
-        u.V = h->V;
-        u.cs = h->cs;
-        u.x = h->x;
-        u.eps = h->eps_work;
-        u.nd = h->nd;
-        u.partials = h->partials;
-        const int slot = prof_begin(h, h->mixed ? KK_NEWTON_UPDATE_F32 : KK_NEWTON_UPDATE_F64);
-        if (h->mixed)
-            k_newton_update<float><<<pointwise_blocks(h->V), kThreads, 0, h->stream>>>(u);
-        else
-            k_newton_update<double><<<pointwise_blocks(h->V), kThreads, 0, h->stream>>>(u);
-        prof_end(h, slot);
-        CK(cudaGetLastError());
-        rc = sync_read(h, true, true);
-        if (rc) return rc;
-        const CGState& c = h->h_cg[0];
-        const double nde = std::sqrt(h->h_nd->de2);
-        const double rel = normE > 0 ? nde / normE : (nde == 0 ? 0.0 : INFINITY);
-        if (it < FFTG_MAX_NEWTON_LOG) {
-            st.cg_per_newton[it] = c.it;
-            st.newton_norm[it] = rel;
-            st.residual[it] = h->h_nd->sig2 > 0 ? std::sqrt(c.gs2 / h->h_nd->sig2) : 0.0;
-            st.cg_relres[it] = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
-            st.cg_status[it] = c.done;
-        }
-        st.cg_iters += c.it;
-        ++it;
-        if (c.done == CG_BREAKDOWN || !std::isfinite(rel)) {
-            status = FFTG_ENAN;
-            break;
-        }
-        if (h->opt.fixed_newton > 0) {
-            if (it >= h->opt.fixed_newton) {
-                converged = true;
-                break;
-            }
-            continue;
-        }
-        if (rel <= tol_newton || nde == 0.0) {
-            converged = true;
-            break;
-        }
-        if (it >= h->opt.max_newton) {
-            status = FFTG_ENOCONV_NEWTON;
-            break;
-        }
-    }
-    st.newton_iters = it;
-    if (newton_iters) *newton_iters = it;
-    if (cg_iters) *cg_iters = st.cg_iters;
-    if (!converged) {
-        st.status = status;
-        return status;
-    }
-    int rc = launch_constitutive(h, Et, h->eps_work, h->sigma, true, nullptr);
-    if (rc) return rc;
-    rc = sync_read(h, false, true);
-    if (rc) return rc;
-    for (int c = 0; c < 6; ++c) sigma_out[c] = h->h_nd->sum[c] / (double)h->V;
-    // commit: the working strain and the updated history become the state
-    std::swap(h->eps_star, h->eps_work);
-    h->hist = 1 - h->hist;
-    for (int c = 0; c < 6; ++c) h->E[c] = Et[c];
-    h->have_tangent = true;
-    st.status = FFTG_OK;
-    return FFTG_OK;
+    int st = 0;
+    return batch_step(h, dE, tol_newton, tol_cg, sigma_out, newton_iters, cg_iters, &st);
 }
 
 int fftg_last_stats(fftg_handle* h, fftg_stats* out) {
     if (!h || !out) return FFTG_EINVAL;
-    *out = h->stats;
+    *out = h->stats[h->sel];
     return FFTG_OK;
 }
 
 int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters) {
     if (!h || !C_out || !(tol_cg > 0)) return FFTG_EINVAL;
     if (h->nrhs != 6) return FFTG_EINVAL;
-    if (!h->have_tangent) return FFTG_ESTATE;
+    const int cell = h->sel;
+    if (!h->have_tangent[cell]) return FFTG_ESTATE;
     const bool f64 = !h->mixed;
+    const size_t ts = f64 ? 8 : 4;
+    const void* tg = (const char*)h->tangent + (size_t)cell * 7 * h->cs * ts;
     const double tol = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
-    set_cg_params(h, 6, tol);
-    CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+    set_cg_params(h, 6, tol, nullptr);
+    CK(cudaMemcpyAsync(h->cg, h->h_cg, h->nf * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
     VecArgs u{};
     u.V = h->V;
     u.cs = h->cs;
-    u.tangent = h->tangent;
+    u.tangent = tg;
     u.cg = h->cg;
     u.nd = h->nd;
     u.partials = h->partials;
@@ -771,18 +987,18 @@ int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters)
     CK(cudaGetLastError());
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     PassArgs a = base_args(h, f64);
-    a.tangent = h->tangent;
+    a.tangent = tg;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_TANRHS_F64 : PK_P1_TANRHS_F32, a, 6));
-    int rc = run_p234(h, f64, -invN3, nullptr, 6);
+    int rc = run_p234(h, f64, -invN3, nullptr, 6, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
     b.out = h->r;
     b.cg = h->cg;
     CK(pass(h, f64 ? PK_P5_RHS_F64_TO_F64 : PK_P5_RHS_F32_TO_F32, b, 6));
-    CK(cudaMemsetAsync(h->x, 0, 6 * 6 * h->cs * (h->mixed ? 4 : 8), h->stream));
-    rc = run_cg(h, 6);
+    CK(cudaMemsetAsync(h->x, 0, 6 * 6 * h->cs * ts, h->stream));
+    rc = run_cg(h, 6, tg, 0);
     if (rc) return rc;
     int total = 0;
     for (int f = 0; f < 6; ++f) {
@@ -812,13 +1028,7 @@ size_t fftg_state_bytes(const fftg_handle* h) {
 
 int fftg_get_state(fftg_handle* h, void* buf, size_t bytes) {
     if (!h || !buf || bytes < fftg_state_bytes(h)) return FFTG_EINVAL;
-    double* d = (double*)buf;
-    std::memcpy(d, h->E, 6 * sizeof(double));
-    CK(copy_field(h, d + 6, false, h->eps_star, true, 8, cudaMemcpyDeviceToHost));
-    CK(copy_field(h, d + 6 + 6 * h->V, false, h->eps_p[h->hist], true, 8, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpyAsync(d + 6 + 12 * h->V, h->epbar[h->hist], h->V * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    return FFTG_OK;
+    return download_cell(h, h->sel, (double*)buf);
 }
 
 int fftg_set_state(fftg_handle* h, const void* buf, size_t bytes) {
@@ -826,24 +1036,19 @@ int fftg_set_state(fftg_handle* h, const void* buf, size_t bytes) {
     const double* d = (const double*)buf;
     for (int c = 0; c < 6; ++c)
         if (!std::isfinite(d[c])) return FFTG_EINVAL;
-    CK(copy_field(h, h->eps_star, true, d + 6, false, 8, cudaMemcpyHostToDevice));
-    CK(copy_field(h, h->eps_p[h->hist], true, d + 6 + 6 * h->V, false, 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpyAsync(h->epbar[h->hist], d + 6 + 12 * h->V, h->V * 8, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    std::memcpy(h->E, d, 6 * sizeof(double));
-    h->have_tangent = false;
-    return FFTG_OK;
+    return upload_cell(h, h->sel, nullptr, d);
 }
 
 int fftg_get_field(fftg_handle* h, int which, double* out) {
     if (!h || !out) return FFTG_EINVAL;
     const size_t V = (size_t)h->V;
+    const int cell = h->sel;
     switch (which) {
         case FFTG_FIELD_STRAIN: {
-            CK(copy_field(h, out, false, h->eps_star, true, 8, cudaMemcpyDeviceToHost));
+            CK(copy_field(h, out, false, cell_field(h->eps_star, h, cell), true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             for (int c = 0; c < 6; ++c)
-                for (size_t v = 0; v < V; ++v) out[c * V + v] += h->E[c];
+                for (size_t v = 0; v < V; ++v) out[c * V + v] += h->E[6 * cell + c];
             return FFTG_OK;
         }
         case FFTG_FIELD_STRESS: {
@@ -851,18 +1056,20 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
             // committed strain, so the trial stress against it is the
             // converged stress (Phi = 0: elastic branch). The tangent of the
             // increment is left untouched.
-            int rc = launch_constitutive(h, h->E, h->eps_star, h->sigma, false, nullptr, false);
+            std::memcpy(h->h_E + 6 * cell, h->E.data() + 6 * cell, 6 * sizeof(double));
+            CK(cudaMemcpyAsync(h->Edev + 6 * cell, h->h_E + 6 * cell, 48, cudaMemcpyHostToDevice, h->stream));
+            int rc = launch_constitutive(h, nullptr, 1, cell, h->eps_star, h->sigma, false, nullptr, false);
             if (rc) return rc;
-            CK(copy_field(h, out, false, h->sigma, true, 8, cudaMemcpyDeviceToHost));
+            CK(copy_field(h, out, false, cell_field(h->sigma, h, cell), true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
         }
         case FFTG_FIELD_EPBAR:
-            CK(cudaMemcpyAsync(out, h->epbar[h->hist], V * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaMemcpyAsync(out, h->epbar + (size_t)cell * h->cs, V * 8, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
         case FFTG_FIELD_EPS_P:
-            CK(copy_field(h, out, false, h->eps_p[h->hist], true, 8, cudaMemcpyDeviceToHost));
+            CK(copy_field(h, out, false, cell_field(h->eps_p, h, cell), true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
         default:
@@ -884,7 +1091,7 @@ int fftg_op_project(fftg_handle* h, int precision, const void* tau, void* out) {
     a.in = in_buf;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_PLAIN_F64 : PK_P1_PLAIN_F32, a, 1));
-    int rc = run_p234(h, f64, invN3, nullptr, 1);
+    int rc = run_p234(h, f64, invN3, nullptr, 1, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
@@ -896,17 +1103,19 @@ int fftg_op_project(fftg_handle* h, int precision, const void* tau, void* out) {
 
 int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps, double* sigma) {
     if (!h) return FFTG_EINVAL;
-    double Et[6];
-    for (int c = 0; c < 6; ++c) Et[c] = h->E[c] + (dE ? dE[c] : 0.0);
+    const int cell = h->sel;
+    for (int c = 0; c < 6; ++c) h->h_E[6 * cell + c] = h->E[6 * cell + c] + (dE ? dE[c] : 0.0);
+    CK(cudaMemcpyAsync(h->Edev + 6 * cell, h->h_E + 6 * cell, 48, cudaMemcpyHostToDevice, h->stream));
     const double* e = h->eps_star;
     if (eps) {
-        CK(copy_field(h, h->eps_work, true, eps, false, 8, cudaMemcpyDeviceToDevice));
+        CK(copy_field(h, cell_field(h->eps_work, h, cell), true, eps, false, 8, cudaMemcpyDeviceToDevice));
         e = h->eps_work;
     }
-    int rc = launch_constitutive(h, Et, e, h->sigma, false, nullptr);
+    int rc = launch_constitutive(h, nullptr, 1, cell, e, h->sigma, false, nullptr);
     if (rc) return rc;
-    if (sigma) CK(copy_field(h, sigma, false, h->sigma, true, 8, cudaMemcpyDeviceToDevice));
-    h->have_tangent = false;
+    if (sigma)
+        CK(copy_field(h, sigma, false, cell_field(h->sigma, h, cell), true, 8, cudaMemcpyDeviceToDevice));
+    h->have_tangent[cell] = 0;
     return FFTG_OK;
 }
 
@@ -915,17 +1124,17 @@ int fftg_op_matvec(fftg_handle* h, int precision, const void* p, void* q, double
     const bool f64 = precision == FFTG_FP64;
     if (f64 == (bool)h->mixed) return FFTG_EINVAL;  // must match the tangent's precision
     const size_t es = f64 ? 8 : 4;
-    set_cg_params(h, 1, 1.0);
+    set_cg_params(h, 1, 1.0, nullptr);
     h->h_cg[0].rr = 1.0;
-    CK(cudaMemcpyAsync(h->cg, h->h_cg, 6 * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->cg, h->h_cg, h->nf * sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
     CK(copy_field(h, h->p, true, p, false, es, cudaMemcpyDeviceToDevice));
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     PassArgs a = base_args(h, f64);
     a.in = h->p;
-    a.tangent = h->tangent;
+    a.tangent = (const char*)h->tangent + (size_t)h->sel * 7 * h->cs * es;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_TAN_F64 : PK_P1_TAN_F32, a, 1));
-    int rc = run_p234(h, f64, invN3, nullptr, 1);
+    int rc = run_p234(h, f64, invN3, nullptr, 1, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;

@@ -39,6 +39,7 @@ struct PassArgs {
     long long fstride;     // real-field stride between fields (elements)
     long long sstride;     // spectrum stride between fields (complex elements)
     long long tstride;     // tangent stride between fields (0: shared)
+    const int* active;     // per field: 0 = skip this field (null: all run)
 };
 
 template <int N, typename T>
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* z = tw + N;  // [3][R][N]
     const int f = blockIdx.z;
+    if (a.active && !a.active[f]) return;
     if (MODE == P1_CG && a.cg[f].done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf = tw + N;  // [S][N][W]
     const int f = blockIdx.z;
+    if (a.active && !a.active[f]) return;
     if (a.cg && a.cg[f].done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf = tw + N;  // [6][N][W]
     const int f = blockIdx.z;
+    if (a.active && !a.active[f]) return;
     if (a.cg && a.cg[f].done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
@@ -449,6 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
     cplx<T>* z = tw + N;  // [3][R][N]
     const int f = blockIdx.z;
     CGState* cg = a.cg ? a.cg + f : nullptr;
+    if (a.active && !a.active[f]) return;
     if (MODE == P5_DOT && cg->done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);

@@ -43,6 +43,14 @@ struct ConstArgs {
     NewtonDev* nd;           // sig2 and sum of sigma
     CGState* cg;             // if set: cg->floor2 from ||sigma||
     double tie;              // plastic iff Phi_trial > tie * sigma_y
+    // Batches of cells: cell = blockIdx.y; per-cell offsets below (0 for a
+    // single cell). Edev [cells][6] replaces E when set; active[cell] == 0
+    // skips the cell.
+    const double* Edev;
+    const int* active;
+    long long cell_fields;   // stride between cells of the [6][cs] fields
+    long long cell_scalar;   // stride of epbar / phase between cells
+    long long cell_tangent;  // stride of the tangent between cells
 };
 
 // Elastic predictor / plastic corrector with linear hardening (n = 1):
@@ -53,21 +61,36 @@ struct ConstArgs {
 // stored as K, 2G_eff, w = sqrt(-b) N (b the N(x)N coefficient, negative).
 template <typename TT>
 __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
+    const int cell = blockIdx.y;
+    if (a.active && !a.active[cell]) return;
     const long long V = a.V, cs = a.cs;
+    const long long of = cell * a.cell_fields, osc = cell * a.cell_scalar;
+    double E[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) E[c] = a.Edev ? a.Edev[6 * cell + c] : a.E[c];
+    const double* eps = a.eps + of;
+    const double* eps_p = a.eps_p + of;
+    const double* epbar = a.epbar + osc;
+    const uint8_t* phase = a.phase + osc;
+    double* sigma = a.sigma ? a.sigma + of : nullptr;
+    double* eps_p_new = a.eps_p_new ? a.eps_p_new + of : nullptr;
+    double* epbar_new = a.epbar_new ? a.epbar_new + osc : nullptr;
+    NewtonDev* nd = a.nd + cell;
+    double* partials = a.partials + (size_t)cell * gridDim.x * 7;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    TT* tg = (TT*)a.tangent;
+    TT* tg = a.tangent ? (TT*)a.tangent + cell * a.cell_tangent : nullptr;
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
          v += (long long)gridDim.x * kThreads) {
-        const int ph = a.phase[v];
+        const int ph = phase[v];
         const double K = a.mats[4 * ph], G = a.mats[4 * ph + 1], sy = a.mats[4 * ph + 2],
                      Hh = a.mats[4 * ph + 3];
         double e[6], ep[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            ep[c] = a.eps_p[c * cs + v];
-            e[c] = a.E[c] + a.eps[c * cs + v] - ep[c];
+            ep[c] = eps_p[c * cs + v];
+            e[c] = E[c] + eps[c * cs + v] - ep[c];
         }
-        const double eb = a.epbar[v];
+        const double eb = epbar[v];
         const double tr = e[0] + e[1] + e[2];
         const double m = tr / 3.0;
         double s[6];
@@ -109,15 +132,15 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
         sig[0] += kt;
         sig[1] += kt;
         sig[2] += kt;
-        if (a.sigma) {
+        if (sigma) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a.sigma[c * cs + v] = sig[c];
+            for (int c = 0; c < 6; ++c) sigma[c * cs + v] = sig[c];
         }
-        if (a.eps_p_new) {
+        if (eps_p_new) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a.eps_p_new[c * cs + v] = ep[c];
+            for (int c = 0; c < 6; ++c) eps_p_new[c * cs + v] = ep[c];
         }
-        if (a.epbar_new) a.epbar_new[v] = eb + dg;
+        if (epbar_new) epbar_new[v] = eb + dg;
         if (tg) {
             tg[v] = (TT)K;
             tg[cs + v] = (TT)g2;
@@ -134,13 +157,13 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
     double part[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) part[j] = block_sum(acc[j]);
-    if (!publish_partials<7>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
+    if (!publish_partials<7>(part, partials, blockIdx.x, gridDim.x, &nd->ticket)) return;
     double tot[7];
-    reduce_partials<7>(a.partials, gridDim.x, &a.nd->ticket, tot);
+    reduce_partials<7>(partials, gridDim.x, &nd->ticket, tot);
     if (threadIdx.x == 0) {
-        a.nd->sig2 = tot[0];
-        for (int c = 0; c < 6; ++c) a.nd->sum[c] = tot[1 + c];
-        if (a.cg) a.cg->floor2 = kRoundoffRel * kRoundoffRel * tot[0];
+        nd->sig2 = tot[0];
+        for (int c = 0; c < 6; ++c) nd->sum[c] = tot[1 + c];
+        if (a.cg) a.cg[cell].floor2 = kRoundoffRel * kRoundoffRel * tot[0];
     }
 }
 
@@ -158,6 +181,8 @@ struct VecArgs {
     long long fstride;
     const void* tangent;
     double* out;       // tangent averages
+    const int* active; // per cell (newton update): 0 = skip
+    long long cell_fields;  // stride between cells of eps (newton update)
 };
 
 // x += alpha p; r -= alpha q; rr = <r, r>; then beta, stopping test.
@@ -240,8 +265,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
 // eps* += x (Algorithm 1, iterative update); nd->de2 = ||x||^2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
+    const int cell = blockIdx.y;
+    if (a.active && !a.active[cell]) return;
     const long long V = a.V, cs = a.cs;
-    const T* x = (const T*)a.x;
+    const T* x = (const T*)a.x + cell * a.fstride;
+    double* eps = a.eps + cell * a.cell_fields;
+    NewtonDev* nd = a.nd + cell;
+    double* partials = a.partials + (size_t)cell * gridDim.x;
     double acc = 0.0;
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
          v += (long long)gridDim.x * kThreads) {
@@ -249,15 +279,15 @@ __global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             d[c] = (double)x[c * cs + v];
-            a.eps[c * cs + v] += d[c];
+            eps[c * cs + v] += d[c];
         }
         acc += frob<double>(d, d);
     }
     double part[1] = {block_sum(acc)};
-    if (!publish_partials<1>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
+    if (!publish_partials<1>(part, partials, blockIdx.x, gridDim.x, &nd->ticket)) return;
     double tot[1];
-    reduce_partials<1>(a.partials, gridDim.x, &a.nd->ticket, tot);
-    if (threadIdx.x == 0) a.nd->de2 = tot[0];
+    reduce_partials<1>(partials, gridDim.x, &nd->ticket, tot);
+    if (threadIdx.x == 0) nd->de2 = tot[0];
 }
 
 template <typename T>

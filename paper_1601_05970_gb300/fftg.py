@@ -59,6 +59,12 @@ class fftg_options(C.Structure):
                 ("nrhs_tangent", C.c_int)]
 
 
+class fftg_result(C.Structure):
+    _fields_ = [("request_id", C.c_longlong), ("session_id", C.c_longlong), ("status", C.c_int),
+                ("newton_iters", C.c_int), ("cg_iters", C.c_int), ("sigma", C.c_double * 6),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
 class fftg_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("cg_iters", C.c_int),
                 ("cg_per_newton", C.c_int * FFTG_MAX_NEWTON_LOG),
@@ -94,6 +100,25 @@ SIGNATURES = {
     "fftg_profile_reset": (C.c_int, [C.c_void_p]),
     "fftg_profile_read": (C.c_int, [C.c_void_p, C.c_int, _D6, C.POINTER(C.c_longlong)]),
     "fftg_launch_count": (C.c_longlong, [C.c_void_p]),
+    "fftg_workspace_size_batch": (C.c_int, [C.c_int, C.c_int, C.POINTER(fftg_options),
+                                            C.POINTER(C.c_size_t)]),
+    "fftg_create_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_uint8),
+                                    C.c_int, C.POINTER(fftg_phase), C.POINTER(fftg_options)]),
+    "fftg_batch_size": (C.c_int, [C.c_void_p]),
+    "fftg_select_cell": (C.c_int, [C.c_void_p, C.c_int]),
+    "fftg_batch_step": (C.c_int, [C.c_void_p, _D6, C.c_double, C.c_double, _D6,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fftg_server_clock": (C.c_double, []),
+    "fftg_server_start": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(fftg_phase), C.POINTER(fftg_options), C.c_double,
+                                    C.c_double]),
+    "fftg_server_submit": (C.c_int, [C.c_void_p, C.c_longlong, C.c_longlong, C.POINTER(C.c_uint8),
+                                     _D6]),
+    "fftg_server_poll": (C.c_int, [C.c_void_p, C.POINTER(fftg_result), C.c_int, C.POINTER(C.c_int),
+                                   C.c_double]),
+    "fftg_server_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_longlong), C.POINTER(C.c_int), _D6]),
+    "fftg_server_stop": (C.c_int, [C.c_void_p]),
     "fftg_constitutive_noalloc": (C.c_int, [C.c_int, _D6, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_int, C.POINTER(fftg_phase), C.c_int,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _D6,
@@ -141,9 +166,11 @@ def workspace_size(N: int, opt: fftg_options) -> int:
 
 
 class Cell:
-    """One periodic cell (handle) whose device memory comes from PyTorch.
+    """A handle of one or more periodic cells whose device memory comes from
+    PyTorch.
 
-    phase: uint8 [N, N, N] (x1 slowest); mats: sequence of (K, G, sigma_y, H).
+    phase: uint8 [N, N, N] (x1 slowest), or [ncells, N, N, N] for a batch;
+    mats: sequence of (K, G, sigma_y, H).
     """
 
     def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
@@ -154,6 +181,8 @@ class Cell:
         lib = load()
         self.N = int(N)
         self.V = self.N ** 3
+        ph_arr = np.asarray(phase, dtype=np.uint8)
+        self.ncells = 1 if ph_arr.ndim == 3 else int(ph_arr.shape[0])
         opt = default_options()
         opt.precision = FFTG_MIXED if precision == "mixed" else FFTG_FP64
         opt.max_newton = max_newton
@@ -165,7 +194,10 @@ class Cell:
         self.device = torch.device(device or "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opt.stream = C.c_void_p(self.stream.cuda_stream)
-        nbytes = workspace_size(self.N, opt)
+        b = C.c_size_t(0)
+        check(lib.fftg_workspace_size_batch(self.N, self.ncells, C.byref(opt), C.byref(b)),
+              "fftg_workspace_size_batch")
+        nbytes = b.value
         self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
         opt.workspace = C.c_void_p((base + 255) & ~255)
@@ -176,8 +208,9 @@ class Cell:
                                       for t in mats])
         h = C.c_void_p()
         with torch.cuda.device(self.device):
-            check(lib.fftg_create(C.byref(h), self.N, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
-                                  len(mats), m, C.byref(opt)), "fftg_create")
+            check(lib.fftg_create_batch(C.byref(h), self.N, self.ncells,
+                                        ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                        len(mats), m, C.byref(opt)), "fftg_create_batch")
         self.h = h
         self._lib = lib
 
@@ -200,6 +233,24 @@ class Cell:
         check(self._lib.fftg_step(self.h, _dptr(dE), tol_newton, tol_cg, _dptr(sig),
                                   C.byref(nn), C.byref(nc)), "fftg_step")
         return sig, nn.value, nc.value
+
+    def batch_step(self, dE, tol_newton, tol_cg):
+        """One increment for every cell: dE [ncells, 6] -> (sigma [ncells, 6],
+        newton [ncells], cg [ncells], status [ncells])."""
+        B = self.ncells
+        dE = np.ascontiguousarray(dE, dtype=np.float64).reshape(B, 6)
+        sig = np.zeros((B, 6))
+        nn = (C.c_int * B)()
+        nc = (C.c_int * B)()
+        st = (C.c_int * B)()
+        rc = self._lib.fftg_batch_step(self.h, dE.ctypes.data_as(_D6), tol_newton, tol_cg,
+                                       sig.ctypes.data_as(_D6), nn, nc, st)
+        if rc not in (FFTG_OK, FFTG_ENOCONV_NEWTON, FFTG_ENAN):
+            check(rc, "fftg_batch_step")
+        return sig, np.array(nn[:]), np.array(nc[:]), np.array(st[:])
+
+    def select(self, cell):
+        check(self._lib.fftg_select_cell(self.h, int(cell)), "fftg_select_cell")
 
     def stats(self):
         s = fftg_stats()
@@ -285,3 +336,76 @@ class Cell:
         check(self._lib.fftg_op_matvec(self.h, prec, C.c_void_p(p.data_ptr()),
                                        C.c_void_p(q.data_ptr()), C.byref(pq)), "fftg_op_matvec")
         return q, pq.value
+
+
+class Server:
+    """Continuous-batching server for one grid size (fftg_server_* calls).
+
+    slots: cells held on the device (size them from the HBM budget with
+    `workspace_size_batch`); sessions beyond that are evicted to host memory.
+    """
+
+    def __init__(self, N, slots, mats, precision="mixed", tol_newton=1e-5, tol_cg=1e-8,
+                 max_newton=50, max_cg=2000, cg_inner_floor=1e-6):
+        lib = load()
+        self.N = int(N)
+        opt = default_options()
+        opt.precision = FFTG_MIXED if precision == "mixed" else FFTG_FP64
+        opt.max_newton = max_newton
+        opt.max_cg = max_cg
+        opt.cg_inner_floor = cg_inner_floor
+        opt.nrhs_tangent = 0
+        m = (fftg_phase * len(mats))(*[fftg_phase(*map(float, (t.as_tuple() if hasattr(t, "as_tuple") else t)))
+                                      for t in mats])
+        h = C.c_void_p()
+        check(lib.fftg_server_start(C.byref(h), self.N, int(slots), len(mats), m, C.byref(opt),
+                                    tol_newton, tol_cg), "fftg_server_start")
+        self.h = h
+        self._lib = lib
+        self._buf = (fftg_result * 256)()
+
+    @staticmethod
+    def clock():
+        return load().fftg_server_clock()
+
+    def submit(self, request_id, session_id, dE, phase=None):
+        dE = np.ascontiguousarray(dE, dtype=np.float64).reshape(6)
+        ph = None
+        if phase is not None:
+            ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8).reshape(-1))
+        check(self._lib.fftg_server_submit(
+            self.h, int(request_id), int(session_id),
+            None if ph is None else ph.ctypes.data_as(C.POINTER(C.c_uint8)), _dptr(dE)),
+            "fftg_server_submit")
+
+    def poll(self, wait_s=0.0):
+        n = C.c_int(0)
+        check(self._lib.fftg_server_poll(self.h, self._buf, 256, C.byref(n), wait_s), "fftg_server_poll")
+        out = []
+        for i in range(n.value):
+            r = self._buf[i]
+            out.append(dict(request_id=r.request_id, session_id=r.session_id, status=r.status,
+                            newton_iters=r.newton_iters, cg_iters=r.cg_iters, sigma=list(r.sigma),
+                            t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done))
+        return out
+
+    def info(self):
+        c, e, r = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
+        mc = C.c_int(0)
+        mb = np.zeros(1)
+        check(self._lib.fftg_server_info(self.h, C.byref(c), C.byref(e), C.byref(r), C.byref(mc),
+                                         mb.ctypes.data_as(_D6)), "fftg_server_info")
+        return dict(completed=c.value, evictions=e.value, restores=r.value,
+                    max_concurrent=mc.value, mean_batch=float(mb[0]))
+
+    def stop(self):
+        if getattr(self, "h", None):
+            rc = self._lib.fftg_server_stop(self.h)
+            self.h = None
+            check(rc, "fftg_server_stop")
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

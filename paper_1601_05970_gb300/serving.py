@@ -1,0 +1,151 @@
+"""Request driver for the continuous-batching servers (fftg_server_*).
+
+An FE^2 macro solver issues RVE increments as its Gauss points need them.
+This driver stands in for it: Poisson arrivals at a given rate, each request
+an increment of Frobenius norm 1e-3 in a random direction for one session
+(an RVE with its own microstructure and history), the grid size of the
+session drawn with given weights. One server per grid size runs its own
+worker thread and stream, so the sizes overlap on the GPU; each server's
+cell count comes from its share of the HBM budget. The driver reports solves
+per second and latency percentiles (submit to result, on the servers'
+clock).
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+
+import numpy as np
+
+from . import fftg
+from . import inputs as I
+
+
+def slots_for_budget(N, budget_bytes, precision="mixed", max_slots=32):
+    """Cells of grid N that fit in `budget_bytes` of device memory."""
+    opt = fftg.default_options()
+    opt.precision = fftg.FFTG_MIXED if precision == "mixed" else fftg.FFTG_FP64
+    opt.nrhs_tangent = 0
+    lib = fftg.load()
+    import ctypes as C
+    one = C.c_size_t(0)
+    fftg.check(lib.fftg_workspace_size_batch(N, 1, C.byref(opt), C.byref(one)), "size")
+    two = C.c_size_t(0)
+    fftg.check(lib.fftg_workspace_size_batch(N, 2, C.byref(opt), C.byref(two)), "size")
+    per = max(1, two.value - one.value)
+    base = one.value - per
+    n = int((budget_bytes - base) // per)
+    return max(1, min(max_slots, n)), per
+
+
+def session_microstructure(N, session_id):
+    """Random hard spheres (radii 3-8, periodic) with a hard fraction drawn in
+    [0.1, 0.4], both seeded by the session id."""
+    rng = I.SplitMix64(10_000 + session_id)
+    frac = 0.1 + 0.3 * rng.uniform()
+    ph, got, _ = I.random_spheres(N, frac, seed=20_000 + session_id)
+    return ph
+
+
+def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
+        sessions_per_N=None, budget_gb=48.0, precision="mixed", seed=5,
+        tol_newton=1e-5, tol_cg=1e-8, max_requests=None):
+    """Poisson arrivals for `duration` seconds at `rate` requests/s.
+
+    Returns a dict with solves/s, p50/p95/p99 latency (ms), per-size counts
+    and server statistics.
+    """
+    weights = np.asarray(weights, dtype=float) / np.sum(weights)
+    budget = budget_gb * 1e9
+    servers, slot_info = {}, {}
+    for N, w in zip(Ns, weights):
+        slots, per = slots_for_budget(N, budget * w, precision)
+        servers[N] = fftg.Server(N, slots, I.TWO_PHASE, precision=precision,
+                                 tol_newton=tol_newton, tol_cg=tol_cg)
+        slot_info[N] = dict(slots=slots, bytes_per_slot=per)
+    if sessions_per_N is None:
+        sessions_per_N = {N: 2 * slot_info[N]["slots"] for N in Ns}
+    # sessions and microstructures are made before the clock starts
+    sess = {}
+    sid = 0
+    for N in Ns:
+        for _ in range(sessions_per_N[N]):
+            sess[sid] = (N, session_microstructure(N, sid))
+            sid += 1
+    by_N = {N: [k for k, v in sess.items() if v[0] == N] for N in Ns}
+    created = set()
+
+    rng = np.random.default_rng(seed)
+    n_req = int(rate * duration * 1.2) + 16
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    sizes = rng.choice(len(Ns), size=n_req, p=weights)
+    picks = rng.random(n_req)
+
+    results = []
+    lock = threading.Lock()
+    stop = threading.Event()
+
+    def collector():
+        while not stop.is_set() or any(len(pending[N]) for N in Ns):
+            got_any = False
+            for N, srv in servers.items():
+                for r in srv.poll(0.0):
+                    with lock:
+                        results.append(r)
+                        pending[N].discard(r["request_id"])
+                    got_any = True
+            if not got_any:
+                time.sleep(0.0005)
+
+    pending = {N: set() for N in Ns}
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = fftg.Server.clock()
+    t_next = t0
+    submitted = 0
+    for i in range(n_req):
+        t_next += gaps[i]
+        if t_next - t0 > duration or (max_requests and submitted >= max_requests):
+            break
+        while True:
+            now = fftg.Server.clock()
+            if now >= t_next:
+                break
+            time.sleep(min(0.002, t_next - now))
+        N = Ns[sizes[i]]
+        pool = by_N[N]
+        s_id = pool[int(picks[i] * len(pool))]
+        dE = I.random_increment(1_000_000 + i, 1e-3)
+        phase = None
+        if s_id not in created:
+            phase = sess[s_id][1]
+            created.add(s_id)
+        with lock:
+            pending[N].add(i)
+        servers[N].submit(i, s_id, dE, phase)
+        submitted += 1
+    t_sub_end = fftg.Server.clock()
+    stop.set()
+    th.join()
+    t_end = fftg.Server.clock()
+    infos = {N: srv.info() for N, srv in servers.items()}
+    for srv in servers.values():
+        srv.stop()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in results]) * 1e3
+    ok = sum(1 for r in results if r["status"] == 0)
+    per_N = {}
+    for N in Ns:
+        l = np.array([r["t_done"] - r["t_submit"] for r in results if sess[r["session_id"]][0] == N]) * 1e3
+        per_N[N] = dict(count=int(l.size), p50_ms=float(np.percentile(l, 50)) if l.size else None,
+                        p99_ms=float(np.percentile(l, 99)) if l.size else None,
+                        slots=slot_info[N]["slots"], sessions=sessions_per_N[N],
+                        evictions=infos[N]["evictions"], max_concurrent=infos[N]["max_concurrent"],
+                        mean_batch=round(infos[N]["mean_batch"], 2))
+    return dict(rate=rate, duration_s=round(t_sub_end - t0, 3), requests=submitted,
+                completed=len(results), ok=ok,
+                solves_per_s=len(results) / max(t_end - t0, 1e-9),
+                p50_ms=float(np.percentile(lat, 50)) if lat.size else None,
+                p95_ms=float(np.percentile(lat, 95)) if lat.size else None,
+                p99_ms=float(np.percentile(lat, 99)) if lat.size else None,
+                per_N=per_N, precision=precision, budget_gb=budget_gb)
