@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--no-tangent", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 comparison, the batched and the serving runs")
+    ap.add_argument("--serve-rate", type=float, default=100.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -174,6 +178,60 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------- ranks
+def rank_seed(rank):
+    """Each rank solves its own cell: the microstructure seed of rank r."""
+    return 2 + 1000 * rank
+
+
+def reduce_over_ranks(dist, dev_ms, wall_ms, units, launches, device):
+    """Job time = the slowest rank (max); work = the sum over ranks. Only the
+    timing is exchanged: the ranks' cells share no data."""
+    import torch
+    t = torch.tensor([dev_ms, wall_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units, float(launches)], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0]), int(u[1])
+
+
+# --------------------------------------------------------------- extras
+def time_to_converged_stress(N, precisions=("mixed", "fp64"), n_inc=4, timed_from=2):
+    """Wall time of increments timed_from.. of the uniaxial path at N^3 for
+    each precision, on fresh cells (no tangent): the first increments are
+    elastic, the timed ones plastic."""
+    import torch
+    from paper_1601_05970_gb300 import fftg
+    from paper_1601_05970_gb300 import inputs as I
+    w = I.workload("spheres243" if N == 243 else "spheres135")
+    out = {}
+    sig_ref = None
+    for prec in precisions:
+        cell = fftg.Cell(N, w["phase"], w["mats"], precision=prec, nrhs_tangent=0)
+        t_tot, iters = 0.0, []
+        for k in range(n_inc):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sig, nn, nc = cell.step(w["dE"][k], w["tol_newton"], w["tol_cg"])
+            torch.cuda.synchronize()
+            if k >= timed_from:
+                t_tot += time.perf_counter() - t0
+                iters.append((nn, nc))
+        out[prec] = dict(seconds=t_tot, increments=n_inc - timed_from, newton_cg=iters,
+                         sigma=[float(v) for v in sig])
+        if sig_ref is None:
+            sig_ref = sig
+        else:
+            out[prec]["max_rel_diff_sigma_vs_" + precisions[0]] = float(
+                np.abs(sig - sig_ref).max() / np.abs(sig_ref).max())
+        cell.close()
+        del cell
+        torch.cuda.empty_cache()
+    if "mixed" in out and "fp64" in out:
+        out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
 # --------------------------------------------------------------- GPU leg
 def main():
     args = parse()
@@ -194,7 +252,7 @@ def main():
     fftg.load()
 
     N = args.N
-    w = I.workload("spheres243" if N == 243 else "spheres135", seed=2 + 1000 * rank)
+    w = I.workload("spheres243" if N == 243 else "spheres135", seed=rank_seed(rank))
     dE = np.array([0.0015, 0, 0, 0, 0, 0]) if N == 243 else np.array([0, 0, 0, 0, 0, 0.001])
     tol_nw, tol_cg = w["tol_newton"], w["tol_cg"]
     cell = fftg.Cell(N, w["phase"], w["mats"], precision=args.precision,
@@ -247,12 +305,8 @@ def main():
     field_iters = acc["cg"] + acc["tangent_cg"]
     units = float(V) * field_iters
     if dist:
-        t = torch.tensor([dev_ms, wall_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([units, float(launches)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        dev_ms, wall_ms = float(t[0]), float(t[1])
-        units, launches = float(u[0]), int(u[1])
+        dev_ms, wall_ms, units, launches = reduce_over_ranks(dist, dev_ms, wall_ms, units, launches,
+                                                              "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -302,6 +356,15 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         v, desc = oracle_sample(N, w["seed"], 3)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if not args.no_extras and world == 1:
+        cell.close()
+        del cell
+        torch.cuda.empty_cache()
+        from paper_1601_05970_gb300 import serving
+        line["time_to_converged_stress"] = time_to_converged_stress(N)
+        rves = serving.batched_workload()
+        line["batched"] = serving.run_batched(rves)
+        line["serving"] = serving.run(args.serve_rate, args.serve_seconds, budget_gb=48.0)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

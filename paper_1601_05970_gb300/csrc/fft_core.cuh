@@ -192,7 +192,7 @@ __device__ __forceinline__ void fwdA(const cplx<T>* src, int ss, cplx<T>* dst, i
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
         cplx<T> y = v[k1];
-        if (N2 > 1 && k1 > 0) y = twmul<-1>(y, tw[(t * k1) % N]);
+        if (N2 > 1 && k1 > 0) y = twmul<-1>(y, tw[t * k1]);  // t*k1 < N1*N2 = N
         dst[(t + N2 * k1) * ds] = y;
     }
 }
@@ -223,7 +223,7 @@ __device__ __forceinline__ void invB(const cplx<T>* src, int ss, cplx<T>* dst, i
 #pragma unroll
     for (int t = 0; t < N2; ++t) {
         cplx<T> z = v[t];
-        if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[(t * k1) % N]);
+        if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[t * k1]);  // t*k1 < N
         dst[(N2 * k1 + t) * ds] = z;
     }
 }

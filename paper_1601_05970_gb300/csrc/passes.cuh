@@ -308,6 +308,11 @@ __global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
     }
 }
 
+// 1/sqrt(x): the hardware reciprocal square root in FP32 (about 2 ulp, far
+// inside the FP32 path's tolerance), correctly rounded operations in FP64.
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+
 // Ghat : tau at frequency (f1, f2, f3), times `scale`, for the 6 complex
 // components (11, 22, 33, 23, 13, 12) held at stride `cs` in shared memory.
 template <typename T>
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
             const int kk = k1 + N1 * k2;
             const int f1 = (kk <= (N - 1) / 2) ? kk : kk - N;
             const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(col) * T(col);
-            const T inv = q2 > T(0) ? T(1) / sqrt(q2) : T(0);
+            const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
             const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(col) * inv;
             // partial tau n: normals (lane 0) or shears (lane 1)
             cplx<T> u0, u1, u2;
@@ -426,7 +431,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
 #pragma unroll
                 for (int t = 0; t < N2; ++t) {
                     cplx<T> z = v[c][t];
-                    if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[(t * k1) % N]);
+                    if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[t * k1]);  // t*k1 < N
                     b[c * N * W + (N2 * k1 + t) * W] = z;
                 }
             }

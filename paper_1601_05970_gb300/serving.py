@@ -2,9 +2,11 @@
 
 An FE^2 macro solver issues RVE increments as its Gauss points need them.
 This driver stands in for it: Poisson arrivals at a given rate, each request
-an increment of Frobenius norm 1e-3 in a random direction for one session
-(an RVE with its own microstructure and history), the grid size of the
-session drawn with given weights. One server per grid size runs its own
+one increment of Frobenius norm 1e-3 for one session (an RVE with its own
+microstructure and history), the grid size of the session drawn with given
+weights. Each session follows its own proportional strain path (a seeded
+random direction), as a Gauss point under monotone macroscopic loading
+does, so its history accumulates plastic strain from request to request. One server per grid size runs its own
 worker thread and stream, so the sizes overlap on the GPU; each server's
 cell count comes from its share of the HBM budget. The driver reports solves
 per second and latency percentiles (submit to result, on the servers'
@@ -116,7 +118,7 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
         N = Ns[sizes[i]]
         pool = by_N[N]
         s_id = pool[int(picks[i] * len(pool))]
-        dE = I.random_increment(1_000_000 + i, 1e-3)
+        dE = I.random_increment(1_000_000 + s_id, 1e-3)
         phase = None
         if s_id not in created:
             phase = sess[s_id][1]
@@ -149,3 +151,63 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
                 p95_ms=float(np.percentile(lat, 95)) if lat.size else None,
                 p99_ms=float(np.percentile(lat, 99)) if lat.size else None,
                 per_N=per_N, precision=precision, budget_gb=budget_gb)
+
+
+def batched_workload(n_rve=256, Ns=(15, 27, 45, 75), seed=1000):
+    """Seeded RVE set: N uniform over Ns, hard fraction uniform in [0.1, 0.4],
+    each RVE with its own microstructure seed (seed + i) and its own
+    proportional strain path (one random direction of norm 1e-3 per
+    increment)."""
+    rng = I.SplitMix64(seed)
+    rves = []
+    for i in range(n_rve):
+        N = Ns[min(len(Ns) - 1, int(rng.uniform() * len(Ns)))]
+        frac = 0.1 + 0.3 * rng.uniform()
+        ph, _, _ = I.random_spheres(N, frac, seed=seed + i)
+        rves.append(dict(N=N, phase=ph, dE=I.random_increment(seed + i, 1e-3), frac=frac))
+    return rves
+
+
+def run_batched(rves, n_inc=5, precision="mixed", tol_newton=1e-5, tol_cg=1e-8):
+    """All RVEs of one grid size form one batch handle (one launch per pass
+    for the whole group); the groups run concurrently, each on its own stream
+    from its own host thread. Returns RVE solves/s and per-group counts."""
+    import torch
+    groups = {}
+    for i, r in enumerate(rves):
+        groups.setdefault(r["N"], []).append(i)
+    cells, streams = {}, {}
+    for N, idx in groups.items():
+        streams[N] = torch.cuda.Stream()
+        ph = np.stack([rves[i]["phase"] for i in idx])
+        cells[N] = fftg.Cell(N, ph, I.TWO_PHASE, precision=precision, nrhs_tangent=0,
+                             stream=streams[N])
+    out = {N: dict(cells=len(idx), newton=0, cg=0, failed=0, seconds=0.0) for N, idx in groups.items()}
+
+    def work(N):
+        idx = groups[N]
+        dE = np.stack([rves[i]["dE"] for i in idx])
+        t0 = time.perf_counter()
+        for _ in range(n_inc):
+            sig, nn, nc, st = cells[N].batch_step(dE, tol_newton, tol_cg)
+            out[N]["newton"] += int(nn.sum())
+            out[N]["cg"] += int(nc.sum())
+            out[N]["failed"] += int((st != 0).sum())
+        torch.cuda.synchronize()
+        out[N]["seconds"] = time.perf_counter() - t0
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=work, args=(N,)) for N in groups]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    for c in cells.values():
+        c.close()
+    n = len(rves) * n_inc
+    return dict(rves=len(rves), increments=n_inc, solves=n, seconds=wall,
+                solves_per_s=n / wall, groups={str(N): v for N, v in sorted(out.items())},
+                precision=precision)
