@@ -90,6 +90,11 @@ typedef struct {
     size_t workspace_bytes;
     int    nrhs_tangent;    /* right-hand sides held for fftg_tangent: 0 (no
                                tangent), or 6 (default 6) */
+    int    cg_graph;        /* 1 (default): run each CG solve as one CUDA graph
+                               whose conditional WHILE node loops on the device
+                               (no host round trip per iteration); 0: enqueue
+                               iterations in chunks from the host. Profiling
+                               (fftg_profile_enable) uses the chunked path. */
 } fftg_options;
 
 /* Per-increment diagnostics of the last fftg_step (Algorithm 1). */

@@ -163,6 +163,19 @@ struct fftg_handle {
     double* h_E = nullptr;
     int* h_active = nullptr;
 
+    unsigned int* guard = nullptr;   // loop-pass counter of the CG graph
+    struct CgGraph {
+        int nf = 0;
+        const void* tangent = nullptr;
+        long long tstride = 0;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long used = 0;
+    };
+    std::vector<CgGraph> graphs;     // small cache of instantiated CG graphs
+    unsigned long long graph_clock = 0;
+    bool graphs_broken = false;      // the driver refused: use the chunked path
+
     std::vector<double> E;           // [B][6] committed
     std::vector<char> have_tangent;  // [B]
     std::vector<fftg_stats> stats;   // [B]
@@ -226,7 +239,7 @@ long long comp_stride(int N) {
 struct Layout {
     size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p, off_eps_p_tr, off_epbar,
         off_epbar_tr, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32,
-        off_tw64, off_partials, off_cg, off_nd, off_E, off_active, off_out36, total;
+        off_tw64, off_partials, off_cg, off_nd, off_E, off_active, off_out36, off_guard, total;
 };
 
 Layout make_layout(int N, int mixed, int nrhs, int B) {
@@ -270,6 +283,7 @@ Layout make_layout(int N, int mixed, int nrhs, int B) {
     L.off_E = take(Bs * 6 * 8);
     L.off_active = take(Bs * 4);
     L.off_out36 = take(36 * 8);
+    L.off_guard = take(64);
     L.total = o;
     return L;
 }
@@ -443,10 +457,125 @@ static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long
     return FFTG_OK;
 }
 
-// Runs CG iterations until every one of the nf solves is done. Iterations
-// are enqueued in chunks; kernels of a finished solve return at entry, so a
-// chunk may overrun the last iteration without effect.
+namespace fftg {
+// Loop condition of the device-resident CG (a conditional WHILE node of a
+// CUDA graph): go on while any of the nf solves is running. `guard` counts
+// the passes of the loop body; past `cap` passes the loop stops whatever the
+// solves report, so the loop always ends.
+__global__ void k_cg_continue(cudaGraphConditionalHandle cond, const CGState* cg, int nf,
+                              unsigned int* guard, unsigned int cap) {
+    if (threadIdx.x != 0) return;
+    bool any = false;
+    for (int f = 0; f < nf; ++f) any = any || (cg[f].done == CG_RUNNING);
+    const unsigned int n = ++(*guard);
+    if (n >= cap) any = false;
+    cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+}  // namespace fftg
+
+// Device-resident CG: one graph whose conditional WHILE node repeats the
+// iteration (the five passes and the update) while any solve is running;
+// k_cg_continue sets the condition on the device, so the host launches the
+// whole solve once and waits once.
+static int build_cg_graph(fftg_handle* h, int nf, const void* tangent, long long tstride,
+                          fftg_handle::CgGraph* g) {
+    g->nf = nf;
+    g->tangent = tangent;
+    g->tstride = tstride;
+    if (cudaGraphCreate(&g->graph, 0) != cudaSuccess) return FFTG_ECUDA;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphConditionalHandleCreate(&cond, g->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return FFTG_ECUDA;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g->graph, nullptr, nullptr, 0, &p) != cudaSuccess) return FFTG_ECUDA;
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess)
+        return FFTG_ECUDA;
+    int rc = launch_cg_iteration(h, nf, tangent, tstride);
+    const unsigned int cap =
+        (unsigned int)((h->opt.fixed_cg > 0 ? h->opt.fixed_cg : h->opt.max_cg) + 4);
+    if (rc == FFTG_OK) {
+        k_cg_continue<<<1, 32, 0, h->stream>>>(cond, h->cg, nf, h->guard, cap);
+        if (cudaGetLastError() != cudaSuccess) rc = FFTG_ECUDA;
+    }
+    cudaGraph_t captured = nullptr;
+    if (cudaStreamEndCapture(h->stream, &captured) != cudaSuccess || rc) return FFTG_ECUDA;
+    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) return FFTG_ECUDA;
+    return FFTG_OK;
+}
+
+static void free_graphs(fftg_handle* h) {
+    for (auto& g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    h->graphs.clear();
+}
+
+// The cached graph for (nf, tangent, tstride), built on first use (at most
+// four are kept; the least recently used is rebuilt on demand).
+static fftg_handle::CgGraph* cg_graph_for(fftg_handle* h, int nf, const void* tangent, long long tstride) {
+    for (auto& g : h->graphs)
+        if (g.nf == nf && g.tangent == tangent && g.tstride == tstride) {
+            g.used = ++h->graph_clock;
+            return &g;
+        }
+    if (h->graphs.size() >= 4) {
+        auto lru = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                    [](const auto& a, const auto& b) { return a.used < b.used; });
+        if (lru->exec) cudaGraphExecDestroy(lru->exec);
+        if (lru->graph) cudaGraphDestroy(lru->graph);
+        h->graphs.erase(lru);
+    }
+    fftg_handle::CgGraph g;
+    const long long launches_before = h->launches;
+    if (build_cg_graph(h, nf, tangent, tstride, &g) != FFTG_OK) {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(h->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(h->stream, &junk);
+            if (junk) cudaGraphDestroy(junk);
+        }
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        cudaGetLastError();
+        h->launches = launches_before;
+        return nullptr;
+    }
+    h->launches = launches_before;  // capture enqueued nothing
+    g.used = ++h->graph_clock;
+    h->graphs.push_back(g);
+    return &h->graphs.back();
+}
+
+// Runs CG iterations until every one of the nf solves is done: as one graph
+// launch (device-resident loop), or, with profiling on or graphs disabled,
+// in chunks enqueued from the host (kernels of a finished solve return at
+// entry, so a chunk may overrun the last iteration without effect).
 static int run_cg(fftg_handle* h, int nf, const void* tangent, long long tstride) {
+    const bool profiling = h->prof && h->prof->on;
+    if (h->opt.cg_graph && !profiling && !h->graphs_broken) {
+        fftg_handle::CgGraph* g = cg_graph_for(h, nf, tangent, tstride);
+        if (g) {
+            CK(cudaMemsetAsync(h->guard, 0, sizeof(unsigned int), h->stream));
+            CK(cudaGraphLaunch(g->exec, h->stream));
+            // one launch of each kernel of an iteration per loop pass
+            CK(cudaMemcpyAsync(h->h_cg, h->cg, nf * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            int maxit = 0;
+            for (int f = 0; f < nf; ++f) maxit = std::max(maxit, h->h_cg[f].it);
+            h->launches += 7LL * (maxit + 1);
+            return FFTG_OK;
+        }
+        h->graphs_broken = true;
+    }
     CK(cudaMemcpyAsync(h->h_cg, h->cg, nf * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     int chunk = 2;
@@ -722,6 +851,7 @@ void fftg_default_options(fftg_options* o) {
     o->max_cg = 2000;
     o->cg_inner_floor = 1e-6;
     o->nrhs_tangent = 6;
+    o->cg_graph = 1;
 }
 
 const char* fftg_version(void) { return "fftg 0.2 (sm_103a)"; }
@@ -812,6 +942,7 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     h->Edev = (double*)(h->ws + L.off_E);
     h->active = (int*)(h->ws + L.off_active);
     h->out36 = (double*)(h->ws + L.off_out36);
+    h->guard = (unsigned int*)(h->ws + L.off_guard);
 
     auto fail = [&](int code) {
         fftg_destroy(h);
@@ -865,6 +996,7 @@ int fftg_create(fftg_handle** out, int N, const uint8_t* phase, int nphase, cons
 void fftg_destroy(fftg_handle* h) {
     if (!h) return;
     if (h->stream || h->ws) cudaStreamSynchronize(h->stream);
+    free_graphs(h);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->h_cg) cudaFreeHost(h->h_cg);
     if (h->h_nd) cudaFreeHost(h->h_nd);

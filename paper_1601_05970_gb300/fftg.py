@@ -56,7 +56,7 @@ class fftg_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_newton", C.c_int), ("max_cg", C.c_int),
                 ("cg_inner_floor", C.c_double), ("fixed_cg", C.c_int), ("fixed_newton", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("nrhs_tangent", C.c_int)]
+                ("nrhs_tangent", C.c_int), ("cg_graph", C.c_int)]
 
 
 class fftg_result(C.Structure):
@@ -175,7 +175,7 @@ class Cell:
 
     def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
                  cg_inner_floor=1e-6, fixed_cg=0, fixed_newton=0, nrhs_tangent=6,
-                 device=None, stream=None):
+                 device=None, stream=None, cg_graph=1):
         import torch
 
         lib = load()
@@ -191,6 +191,7 @@ class Cell:
         opt.fixed_cg = fixed_cg
         opt.fixed_newton = fixed_newton
         opt.nrhs_tangent = nrhs_tangent
+        opt.cg_graph = cg_graph
         self.device = torch.device(device or "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -346,7 +347,7 @@ class Server:
     """
 
     def __init__(self, N, slots, mats, precision="mixed", tol_newton=1e-5, tol_cg=1e-8,
-                 max_newton=50, max_cg=2000, cg_inner_floor=1e-6):
+                 max_newton=50, max_cg=2000, cg_inner_floor=1e-6, cg_graph=1):
         lib = load()
         self.N = int(N)
         opt = default_options()
@@ -355,6 +356,7 @@ class Server:
         opt.max_cg = max_cg
         opt.cg_inner_floor = cg_inner_floor
         opt.nrhs_tangent = 0
+        opt.cg_graph = cg_graph
         m = (fftg_phase * len(mats))(*[fftg_phase(*map(float, (t.as_tuple() if hasattr(t, "as_tuple") else t)))
                                       for t in mats])
         h = C.c_void_p()

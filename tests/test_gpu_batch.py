@@ -90,3 +90,23 @@ def test_batch_failed_cell_is_not_committed():
     assert st[1] == fftg.FFTG_ENOCONV_NEWTON
     assert np.array_equal(batch.get_state(), before)
     batch.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_loop_equals_host_chunked_loop(prec):
+    # the device-resident CG (graph with a conditional WHILE node) runs the
+    # same kernels in the same order as the host-chunked loop: identical bits
+    N = 27
+    ph = _phases(N, [51, 52])
+    a = fftg.Cell(N, ph, I.TWO_PHASE, precision=prec, nrhs_tangent=0, cg_graph=1)
+    b = fftg.Cell(N, ph, I.TWO_PHASE, precision=prec, nrhs_tangent=0, cg_graph=0)
+    dE = np.zeros((2, 6))
+    dE[0, 5] = 0.0015
+    dE[1, 0] = 0.0015
+    for _ in range(3):
+        ra = a.batch_step(dE, 1e-5, 1e-8)
+        rb = b.batch_step(dE, 1e-5, 1e-8)
+        assert np.array_equal(ra[0], rb[0])
+        assert np.array_equal(ra[1], rb[1]) and np.array_equal(ra[2], rb[2])
+    a.close()
+    b.close()

@@ -74,11 +74,11 @@ def test_server_same_alone_and_in_mix(prec):
 
 def test_server_admits_while_busy():
     # a request submitted while another is in flight joins the running batch
-    N = 27
+    N = 75
     ph = [I.random_spheres(N, 0.3, 60 + s)[0] for s in range(2)]
     srv = fftg.Server(N, 2, I.TWO_PHASE, precision="mixed")
     srv.submit(0, 0, [0, 0, 0, 0, 0, 0.004], ph[0])   # plastic: several Newton rounds
-    time.sleep(0.02)
+    time.sleep(0.002)
     srv.submit(1, 1, [0, 0, 0, 0, 0, 0.004], ph[1])
     res = _collect(srv, 2)
     info = srv.info()
