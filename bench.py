@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, the batched and the serving runs")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="enqueue CG iterations from the host instead of the graph loop")
     ap.add_argument("--serve-rate", type=float, default=100.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     return ap.parse_args()
@@ -232,6 +234,61 @@ def time_to_converged_stress(N, precisions=("mixed", "fp64"), n_inc=4, timed_fro
     return out
 
 
+def cufft_matvec_line(N, iters=10):
+    """Comparison line: q = G(C:p) with library FFTs (cuFFT through
+    torch.fft rfftn/irfftn, FP32) and separate elementwise kernels for C:p
+    and Ghat, on the same fields and compact tangent as the fused path.
+    Returns ms per matvec (CUDA events, after warm-up)."""
+    import torch
+    dev = "cuda"
+    g = torch.Generator(device=dev).manual_seed(0)
+    p = torch.randn(6, N, N, N, device=dev, generator=g)
+    K = torch.full((N, N, N), 0.833, device=dev)
+    g2 = torch.full((N, N, N), 0.772, device=dev)
+    w = 0.01 * torch.randn(5, N, N, N, device=dev, generator=g)
+    k = torch.fft.fftfreq(N, d=1.0 / N, device=dev)
+    k3 = torch.fft.rfftfreq(N, d=1.0 / N, device=dev)
+    K1, K2, K3 = torch.meshgrid(k, k, k3, indexing="ij")
+    q2 = K1 * K1 + K2 * K2 + K3 * K3
+    inv = torch.where(q2 > 0, torch.rsqrt(torch.clamp(q2, min=1.0)), torch.zeros_like(q2))
+    n = torch.stack([K1 * inv, K2 * inv, K3 * inv])
+    scale = 1.0 / N ** 3
+
+    def matvec(p):
+        w0, w1, w23, w13, w12 = w
+        w2 = -(w0 + w1)
+        tr = p[0] + p[1] + p[2]
+        m = tr / 3.0
+        wp = w0 * p[0] + w1 * p[1] + w2 * p[2] + 2.0 * (w23 * p[3] + w13 * p[4] + w12 * p[5])
+        s = torch.stack([K * tr + g2 * (p[0] - m) - wp * w0, K * tr + g2 * (p[1] - m) - wp * w1,
+                         K * tr + g2 * (p[2] - m) - wp * w2, g2 * p[3] - wp * w23,
+                         g2 * p[4] - wp * w13, g2 * p[5] - wp * w12])
+        t = torch.fft.rfftn(s, dim=(1, 2, 3))
+        v0 = n[0] * t[0] + n[1] * t[5] + n[2] * t[4]
+        v1 = n[0] * t[5] + n[1] * t[1] + n[2] * t[3]
+        v2 = n[0] * t[4] + n[1] * t[3] + n[2] * t[2]
+        sn = n[0] * v0 + n[1] * v1 + n[2] * v2
+        o = torch.stack([2 * n[0] * v0 - n[0] * n[0] * sn, 2 * n[1] * v1 - n[1] * n[1] * sn,
+                         2 * n[2] * v2 - n[2] * n[2] * sn, n[1] * v2 + n[2] * v1 - n[1] * n[2] * sn,
+                         n[0] * v2 + n[2] * v0 - n[0] * n[2] * sn, n[0] * v1 + n[1] * v0 - n[0] * n[1] * sn])
+        q = torch.fft.irfftn(o * scale, s=(N, N, N), dim=(1, 2, 3)) * N ** 3
+        return q, (p * q).sum()
+
+    for _ in range(3):
+        matvec(p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        matvec(p)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    del p, K, g2, w, n, q2, inv, K1, K2, K3
+    torch.cuda.empty_cache()
+    return ms
+
+
 # --------------------------------------------------------------- GPU leg
 def main():
     args = parse()
@@ -256,7 +313,8 @@ def main():
     dE = np.array([0.0015, 0, 0, 0, 0, 0]) if N == 243 else np.array([0, 0, 0, 0, 0, 0.001])
     tol_nw, tol_cg = w["tol_newton"], w["tol_cg"]
     cell = fftg.Cell(N, w["phase"], w["mats"], precision=args.precision,
-                     nrhs_tangent=0 if args.no_tangent else 6)
+                     nrhs_tangent=0 if args.no_tangent else 6,
+                     cg_graph=0 if args.no_graph else 1)
     stream = cell.stream
     V = N ** 3
 
@@ -361,6 +419,12 @@ def main():
         del cell
         torch.cuda.empty_cache()
         from paper_1601_05970_gb300 import serving
+        fused = sum(line["kernels"].get(k, {"ms": 0.0})["ms"] for k in
+                    ("p1_cg_f32", "p2_f32", "p3_f32", "p4_f32", "p5_dot_f32")) / max(field_iters, 1)
+        line["cufft_line"] = {"matvec_ms": cufft_matvec_line(N), "fused_matvec_ms": fused,
+                              "what": "q = G(C:p) at N^3 FP32: cuFFT rfftn/irfftn via torch.fft with "
+                                      "separate elementwise C:p and Ghat kernels, vs the fused passes "
+                                      "P1-P5 per CG field-iteration in the timed region"}
         line["time_to_converged_stress"] = time_to_converged_stress(N)
         rves = serving.batched_workload()
         line["batched"] = serving.run_batched(rves)

@@ -42,6 +42,64 @@ struct PassArgs {
     const int* active;     // per field: 0 = skip this field (null: all run)
 };
 
+// Tuning of the elementwise phases of P1 and P5: voxels per lane (1, 2 or 4,
+// moved as one vector per component) and the minimum resident blocks per SM
+// (an upper bound on registers). Chosen by timing the variants at 243^3:
+// P1 with 4 voxels per lane and 3 blocks per SM (80 registers) took 0.355 ms
+// per CG iteration against 0.44 ms (1 block) and 0.39 ms (2 voxels, 4 blocks):
+// its 19 loads per voxel need many bytes in flight. P5 with 2 voxels per
+// lane and 4 blocks per SM took 0.223 ms against 0.245 (1 or 4 voxels) and
+// 0.31-0.38 ms with 2 blocks per SM.
+#ifndef FFTG_P1_VW
+#define FFTG_P1_VW 4
+#endif
+#ifndef FFTG_P1_MINB
+#define FFTG_P1_MINB 3
+#endif
+#ifndef FFTG_P5_VW
+#define FFTG_P5_VW 2
+#endif
+#ifndef FFTG_P5_MINB
+#define FFTG_P5_MINB 4
+#endif
+
+template <typename T, int W>
+struct VecN;
+template <typename T>
+struct VecN<T, 1> {
+    using type = T;
+};
+template <>
+struct VecN<float, 2> {
+    using type = float2;
+};
+template <>
+struct VecN<float, 4> {
+    using type = float4;
+};
+template <>
+struct VecN<double, 2> {
+    using type = double2;
+};
+
+template <int W, typename T>
+__device__ __forceinline__ void ldv(const T* p, T (&v)[W]) {
+    using VT = typename VecN<T, W>::type;
+    const VT t = *reinterpret_cast<const VT*>(p);
+    const T* e = reinterpret_cast<const T*>(&t);
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = e[k];
+}
+template <int W, typename T>
+__device__ __forceinline__ void stv(T* p, const T (&v)[W]) {
+    using VT = typename VecN<T, W>::type;
+    VT t;
+    T* e = reinterpret_cast<T*>(&t);
+#pragma unroll
+    for (int k = 0; k < W; ++k) e[k] = v[k];
+    *reinterpret_cast<VT*>(p) = t;
+}
+
 template <int N, typename T>
 struct Cfg {
     static constexpr int H = (N + 1) / 2;
@@ -55,7 +113,8 @@ struct Cfg {
     // are a whole number of 16-byte vectors
     static constexpr int R0 = fl2(ROW_BUDGET / (3 * N * CS));
     static constexpr int R = R0 < 4 ? 4 : R0;
-    static constexpr int VW = 16 / (int)sizeof(T);  // elements per 16-byte vector
+    // voxels per lane in P1's elementwise phase (FP64: at most 2 = 16 bytes)
+    static constexpr int VW = (sizeof(T) == 8 && FFTG_P1_VW > 2) ? 2 : FFTG_P1_VW;
     static constexpr int W3 = fl2(BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(BUDGET / (6 * N * CS));
     static constexpr int W2 = (CS == 8) ? 32 : 16;                            // columns, P2/P4
     static constexpr int S2 = fl2(BUDGET / (N * W2 * CS)) > 16 ? 16 : fl2(BUDGET / (N * W2 * CS));
@@ -110,29 +169,9 @@ struct Vec16<double> {
     using type = double2;
 };
 
-// 16-byte vector load/store of VW consecutive elements
-template <typename T>
-__device__ __forceinline__ void ld16(const T* p, T (&v)[16 / sizeof(T)]) {
-    using VT = typename Vec16<T>::type;
-    const VT t = *reinterpret_cast<const VT*>(p);
-    static_assert(sizeof(VT) == 16, "16-byte vectors");
-    const T* e = reinterpret_cast<const T*>(&t);
-#pragma unroll
-    for (int k = 0; k < (int)(16 / sizeof(T)); ++k) v[k] = e[k];
-}
-template <typename T>
-__device__ __forceinline__ void st16(T* p, const T (&v)[16 / sizeof(T)]) {
-    using VT = typename Vec16<T>::type;
-    VT t;
-    T* e = reinterpret_cast<T*>(&t);
-#pragma unroll
-    for (int k = 0; k < (int)(16 / sizeof(T)); ++k) e[k] = v[k];
-    *reinterpret_cast<VT*>(p) = t;
-}
-
 // ----------------------------------------------------------------------- P1
 template <int N, typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 1) k_p1(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -157,11 +196,13 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
         beta = (T)a.cg[f].beta;
         first = a.cg[f].it == 0;
     }
-    // Elementwise phase on 16-byte vectors. A block's R rows are R*N
-    // contiguous elements per component starting at a multiple of VW; in the
-    // last block the vector that straddles the end of the grid reads and
-    // writes only the padding of the component (cs >= N^3 + 4), and its
-    // lanes past the grid belong to rows that the FFT stages skip.
+    // Elementwise phase: each lane takes VW consecutive voxels of the block's
+    // R rows (R*N contiguous elements per component, R a multiple of 4, so
+    // a block starts on a vector boundary) and loads them as one vector per
+    // component; more voxels per lane keep more loads in flight. In the last
+    // block the vector that straddles the end of the grid reads and writes
+    // only the padding of the component (cs >= N^3 + 4), and its lanes past
+    // the grid belong to rows that the FFT stages skip.
     constexpr int VW = C::VW;
     for (int j = tid; j < (R * N) / VW; j += kThreads) {
         const int i0 = j * VW;
@@ -174,14 +215,14 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
                 T* pp = (T*)a.aux2 + f * a.fstride;
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    ld16<T>(r + c * cs + v0, p[c]);
+                    ldv<VW, T>(r + c * cs + v0, p[c]);
                     if (!first) {
                         T po[VW];
-                        ld16<T>(pp + c * cs + v0, po);
+                        ldv<VW, T>(pp + c * cs + v0, po);
 #pragma unroll
                         for (int e = 0; e < VW; ++e) p[c][e] += beta * po[e];
                     }
-                    st16<T>(pp + c * cs + v0, p[c]);
+                    stv<VW, T>(pp + c * cs + v0, p[c]);
                 }
             } else if (MODE == P1_TANRHS) {
 #pragma unroll
@@ -190,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
                     for (int e = 0; e < VW; ++e) p[c][e] = (c == f) ? T(1) : T(0);
             } else {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) ld16<T>(in + c * cs + v0, p[c]);
+                for (int c = 0; c < 6; ++c) ldv<VW, T>(in + c * cs + v0, p[c]);
             }
             if (MODE == P1_PLAIN) {
 #pragma unroll
@@ -200,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_p1(PassArgs a) {
             } else {
                 T t7[7][VW];
 #pragma unroll
-                for (int k = 0; k < 7; ++k) ld16<T>(tg + k * cs + v0, t7[k]);
+                for (int k = 0; k < 7; ++k) ldv<VW, T>(tg + k * cs + v0, t7[k]);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
                     const T pe[6] = {p[0][e], p[1][e], p[2][e], p[3][e], p[4][e], p[5][e]};
@@ -398,31 +439,31 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
             const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(col) * T(col);
             const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
             const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(col) * inv;
-            // partial tau n: normals (lane 0) or shears (lane 1)
-            cplx<T> u0, u1, u2;
-            if (half == 0) {
-                u0 = n0 * v[0][k2];
-                u1 = n1 * v[1][k2];
-                u2 = n2 * v[2][k2];
-            } else {  // v[0] = 23, v[1] = 13, v[2] = 12
-                u0 = n1 * v[2][k2] + n2 * v[1][k2];
-                u1 = n0 * v[2][k2] + n2 * v[0][k2];
-                u2 = n0 * v[1][k2] + n1 * v[0][k2];
-            }
-            const cplx<T> t0 = mk(__shfl_xor_sync(0xffffffffu, u0.x, 1), __shfl_xor_sync(0xffffffffu, u0.y, 1));
-            const cplx<T> t1 = mk(__shfl_xor_sync(0xffffffffu, u1.x, 1), __shfl_xor_sync(0xffffffffu, u1.y, 1));
-            const cplx<T> t2 = mk(__shfl_xor_sync(0xffffffffu, u2.x, 1), __shfl_xor_sync(0xffffffffu, u2.y, 1));
-            const cplx<T> t0s = u0 + t0, t1s = u1 + t1, t2s = u2 + t2;  // tau n
-            const cplx<T> sn = n0 * t0s + n1 * t1s + n2 * t2s;           // n . tau n
-            if (half == 0) {
-                v[0][k2] = scale * (T(2) * n0 * t0s - (n0 * n0) * sn);
-                v[1][k2] = scale * (T(2) * n1 * t1s - (n1 * n1) * sn);
-                v[2][k2] = scale * (T(2) * n2 * t2s - (n2 * n2) * sn);
-            } else {
-                v[0][k2] = scale * (n1 * t2s + n2 * t1s - (n1 * n2) * sn);
-                v[1][k2] = scale * (n0 * t2s + n2 * t0s - (n0 * n2) * sn);
-                v[2][k2] = scale * (n0 * t1s + n1 * t0s - (n0 * n1) * sn);
-            }
+            // Branch-free across the lane pair. Lane 0 holds (11, 22, 33),
+            // lane 1 (23, 13, 12); with A = diag(n) on lane 0 and
+            // A = [[0, n2, n1], [n2, 0, n0], [n1, n0, 0]] on lane 1, each lane's
+            // share of tau n is u = A v; t = u0 + u1 (shuffle) is tau n,
+            // s = n . t, and the lane's outputs are w A t - D s with w = 2,
+            // D = (n0^2, n1^2, n2^2) on lane 0 and w = 1, D = (n1 n2, n0 n2,
+            // n0 n1) on lane 1 (the closed form n(x)t + t(x)n - s n(x)n).
+            const bool sh = half != 0;
+            const T a00 = sh ? T(0) : n0, a01 = sh ? n2 : T(0), a02 = sh ? n1 : T(0);
+            const T a10 = sh ? n2 : T(0), a11 = sh ? T(0) : n1, a12 = sh ? n0 : T(0);
+            const T a20 = sh ? n1 : T(0), a21 = sh ? n0 : T(0), a22 = sh ? T(0) : n2;
+            const cplx<T> u0 = a00 * v[0][k2] + a01 * v[1][k2] + a02 * v[2][k2];
+            const cplx<T> u1 = a10 * v[0][k2] + a11 * v[1][k2] + a12 * v[2][k2];
+            const cplx<T> u2 = a20 * v[0][k2] + a21 * v[1][k2] + a22 * v[2][k2];
+            const cplx<T> t0 = u0 + mk(__shfl_xor_sync(0xffffffffu, u0.x, 1), __shfl_xor_sync(0xffffffffu, u0.y, 1));
+            const cplx<T> t1 = u1 + mk(__shfl_xor_sync(0xffffffffu, u1.x, 1), __shfl_xor_sync(0xffffffffu, u1.y, 1));
+            const cplx<T> t2 = u2 + mk(__shfl_xor_sync(0xffffffffu, u2.x, 1), __shfl_xor_sync(0xffffffffu, u2.y, 1));
+            const cplx<T> sn = n0 * t0 + n1 * t1 + n2 * t2;  // n . tau n
+            const T w = (sh ? T(1) : T(2)) * scale;
+            const T d0 = scale * (sh ? n1 * n2 : n0 * n0);
+            const T d1 = scale * (sh ? n0 * n2 : n1 * n1);
+            const T d2 = scale * (sh ? n0 * n1 : n2 * n2);
+            v[0][k2] = w * (a00 * t0 + a01 * t1 + a02 * t2) - d0 * sn;
+            v[1][k2] = w * (a10 * t0 + a11 * t1 + a12 * t2) - d1 * sn;
+            v[2][k2] = w * (a20 * t0 + a21 * t1 + a22 * t2) - d2 * sn;
         }
         if (valid) {
 #pragma unroll
@@ -449,7 +490,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
 // T: FFT precision; TO: output real type (P5_RHS writes the CG residual r
 // in the inner precision).
 template <int N, typename T, int MODE, typename TO>
-__global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 1) k_p5(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -498,36 +539,36 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
     TO* out = (TO*)a.out + f * a.fstride;
     T acc0 = T(0);
     double acc1 = 0.0;
-    // Vectors of VO output elements (16 bytes of TO); lanes past the grid in
-    // the last block write only component padding and are left out of the
-    // sums.
-    constexpr int VO = 16 / (int)sizeof(TO);
+    // VO voxels per lane (FFTG_P5_VW, at most 16 bytes of TO): one vector
+    // per component for q and p. With VO = 1 the tile reads are free of bank
+    // conflicts. Lanes past the grid in the last block write only component
+    // padding and are left out of the sums.
+    constexpr int VO = (FFTG_P5_VW * (int)sizeof(TO) > 16) ? 16 / (int)sizeof(TO) : FFTG_P5_VW;
     for (int j = tid; j < (R * N) / VO; j += kThreads) {
         const int i0 = j * VO;
         if (i0 >= nel) continue;
         const long long v0 = base + i0;
         TO q[6][VO];
+        T qd[6][VO];
 #pragma unroll
         for (int e = 0; e < VO; ++e) {
             const cplx<T> z0 = z[i0 + e], z1 = z[R * N + i0 + e], z2 = z[2 * R * N + i0 + e];
-            q[0][e] = (TO)z0.x;
-            q[1][e] = (TO)z0.y;
-            q[2][e] = (TO)z1.x;
-            q[3][e] = (TO)z1.y;
-            q[4][e] = (TO)z2.x;
-            q[5][e] = (TO)z2.y;
-            if (MODE == P5_RHS && i0 + e < nel) {
-                const T qd[6] = {z0.x, z0.y, z1.x, z1.y, z2.x, z2.y};
-                acc1 += (double)frob<T>(qd, qd);
-            }
+            qd[0][e] = z0.x;
+            qd[1][e] = z0.y;
+            qd[2][e] = z1.x;
+            qd[3][e] = z1.y;
+            qd[4][e] = z2.x;
+            qd[5][e] = z2.y;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) q[c][e] = (TO)qd[c][e];
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) st16<TO>(out + c * cs + v0, q[c]);
+        for (int c = 0; c < 6; ++c) stv<VO, TO>(out + c * cs + v0, q[c]);
         if (MODE == P5_DOT) {
             const TO* p = (const TO*)a.aux + f * a.fstride;
             TO pv[6][VO];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) ld16<TO>(p + c * cs + v0, pv[c]);
+            for (int c = 0; c < 6; ++c) ldv<VO, TO>(p + c * cs + v0, pv[c]);
 #pragma unroll
             for (int e = 0; e < VO; ++e) {
                 if (i0 + e < nel) {
@@ -540,7 +581,9 @@ __global__ void __launch_bounds__(kThreads) k_p5(PassArgs a) {
 #pragma unroll
             for (int e = 0; e < VO; ++e) {
                 if (i0 + e < nel) {
+                    const T qde[6] = {qd[0][e], qd[1][e], qd[2][e], qd[3][e], qd[4][e], qd[5][e]};
                     const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
+                    acc1 += (double)frob<T>(qde, qde);
                     acc0 += (T)frob<TO>(qe, qe);
                 }
             }

@@ -211,3 +211,23 @@ def run_batched(rves, n_inc=5, precision="mixed", tol_newton=1e-5, tol_cg=1e-8):
     return dict(rves=len(rves), increments=n_inc, solves=n, seconds=wall,
                 solves_per_s=n / wall, groups={str(N): v for N, v in sorted(out.items())},
                 precision=precision)
+
+
+def main(argv=None):
+    """Rate sweep: one JSON line per Poisson rate (requests/s)."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="continuous-batching RVE serving sweep")
+    ap.add_argument("--rates", default="50,100,200,500")
+    ap.add_argument("--seconds", type=float, default=10.0)
+    ap.add_argument("--budget-gb", type=float, default=48.0)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    args = ap.parse_args(argv)
+    fftg.load()
+    for rate in [float(r) for r in args.rates.split(",")]:
+        res = run(rate, args.seconds, budget_gb=args.budget_gb, precision=args.precision)
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()
