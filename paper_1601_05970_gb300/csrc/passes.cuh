@@ -63,6 +63,16 @@ struct PassArgs {
 #define FFTG_P5_MINB 4
 #endif
 
+// Block shapes: P3 columns per block (0 = as many as fit ~100 KB of shared
+// memory, at most 32) and P1/P5 rows per block (0 = as many as fit ~50 KB,
+// at least 4).
+#ifndef FFTG_P3_W
+#define FFTG_P3_W 0
+#endif
+#ifndef FFTG_ROWS
+#define FFTG_ROWS 0
+#endif
+
 template <typename T, int W>
 struct VecN;
 template <typename T>
@@ -111,11 +121,12 @@ struct Cfg {
     }
     // rows per block in P1/P5: a power of two >= 4, so that a block's rows
     // are a whole number of 16-byte vectors
-    static constexpr int R0 = fl2(ROW_BUDGET / (3 * N * CS));
+    static constexpr int R0 = FFTG_ROWS > 0 ? FFTG_ROWS : fl2(ROW_BUDGET / (3 * N * CS));
     static constexpr int R = R0 < 4 ? 4 : R0;
     // voxels per lane in P1's elementwise phase (FP64: at most 2 = 16 bytes)
     static constexpr int VW = (sizeof(T) == 8 && FFTG_P1_VW > 2) ? 2 : FFTG_P1_VW;
-    static constexpr int W3 = fl2(BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(BUDGET / (6 * N * CS));
+    static constexpr int W3a = fl2(BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(BUDGET / (6 * N * CS));
+    static constexpr int W3 = (FFTG_P3_W > 0 && FFTG_P3_W < W3a) ? FFTG_P3_W : W3a;
     static constexpr int W2 = (CS == 8) ? 32 : 16;                            // columns, P2/P4
     static constexpr int S2 = fl2(BUDGET / (N * W2 * CS)) > 16 ? 16 : fl2(BUDGET / (N * W2 * CS));
     static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
@@ -390,7 +401,8 @@ __device__ __forceinline__ void apply_ghat(cplx<T>* b, int cs, int f1, int f2, i
 // a (column, k1): lane 0 holds the normal components (11, 22, 33), lane 1
 // the shear ones (23, 13, 12); they exchange their parts of tau n by shuffle.
 template <int N, typename T>
-__global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T3 <= 512) ? 2 : 1) k_p3(PassArgs a) {
+__global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T3 <= 512)
+                                                      ? (Cfg<N, T>::T3 <= 256 ? 4 : 2) : 1) k_p3(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int H = C::H, W = C::W3, NT = C::T3;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
