@@ -47,10 +47,12 @@ def bytes_per_voxel(N):
     s32 = 6 * 8 * H / N
     s64 = 2 * s32
     return {
-        "p1_cg_f32": 24 + 24 + 24 + 28 + s32,      # r, p in; p out; tangent; spectrum out
+        # r, p, x in; p, x out; tangent; spectrum out (steady state: the
+        # first iteration of a solve reads no p or x)
+        "p1_cg_f32": 5 * 24 + 28 + s32,
         "p2_f32": 2 * s32, "p3_f32": 2 * s32, "p4_f32": 2 * s32,
         "p5_dot_f32": s32 + 24 + 24,               # spectrum in; q out; p in
-        "cg_update_f32": 4 * 24 + 2 * 24,          # x, p, r, q in; x, r out
+        "cg_update_f32": 3 * 24,                   # r, q in; r out
         "p1_tanrhs_f32": 28 + s32,
         "p5_rhs_f32_to_f32": s32 + 24,
         "p1_plain_f64": 48 + s64, "p2_f64": 2 * s64, "p3_f64": 2 * s64, "p4_f64": 2 * s64,

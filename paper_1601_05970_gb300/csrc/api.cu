@@ -89,7 +89,8 @@ using namespace fftg;
 namespace {
 enum : int {
     KK_CONSTITUTIVE_F32 = PK_COUNT, KK_CONSTITUTIVE_F64, KK_CG_UPDATE_F32, KK_CG_UPDATE_F64,
-    KK_NEWTON_UPDATE_F32, KK_NEWTON_UPDATE_F64, KK_TANGENT_FLOOR, KK_TANGENT_AVERAGE, KK_COUNT
+    KK_NEWTON_UPDATE_F32, KK_NEWTON_UPDATE_F64, KK_TANGENT_FLOOR, KK_TANGENT_AVERAGE,
+    KK_CG_FINISH_F32, KK_CG_FINISH_F64, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "p1_plain_f64", "p1_plain_f32", "p1_tan_f64", "p1_tan_f32", "p1_cg_f64", "p1_cg_f32",
@@ -97,7 +98,7 @@ const char* const kKindNames[KK_COUNT] = {
     "p5_plain_f64", "p5_plain_f32", "p5_dot_f64", "p5_dot_f32", "p5_rhs_f64_to_f64",
     "p5_rhs_f64_to_f32", "p5_rhs_f32_to_f32", "constitutive_f32", "constitutive_f64",
     "cg_update_f32", "cg_update_f64", "newton_update_f32", "newton_update_f64", "tangent_floor",
-    "tangent_average"};
+    "tangent_average", "cg_finish_f32", "cg_finish_f64"};
 
 // Ring of event pairs around the handle's launches; drained at every read.
 struct Prof {
@@ -423,6 +424,7 @@ static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long
     PassArgs a = base_args(h, f64);
     a.aux = h->r;
     a.aux2 = h->p;
+    a.aux3 = h->x;
     a.tangent = tangent;
     a.tstride = tstride;
     a.out = h->spec;
@@ -555,6 +557,27 @@ static fftg_handle::CgGraph* cg_graph_for(fftg_handle* h, int nf, const void* ta
     return &h->graphs.back();
 }
 
+// x += alpha p for the solves whose last update left that step pending.
+static int launch_cg_finish(fftg_handle* h, int nf) {
+    const bool f64 = !h->mixed;
+    VecArgs u{};
+    u.V = h->V;
+    u.cs = h->cs;
+    u.x = h->x;
+    u.p = h->p;
+    u.cg = h->cg;
+    u.fstride = 6 * h->cs;
+    dim3 g(vector_blocks(6 * h->cs, f64 ? 8 : 4), 1, nf);
+    const int slot = prof_begin(h, f64 ? KK_CG_FINISH_F64 : KK_CG_FINISH_F32);
+    if (f64)
+        k_cg_finish<double><<<g, kThreads, 0, h->stream>>>(u);
+    else
+        k_cg_finish<float><<<g, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    return FFTG_OK;
+}
+
 // Runs CG iterations until every one of the nf solves is done: as one graph
 // launch (device-resident loop), or, with profiling on or graphs disabled,
 // in chunks enqueued from the host (kernels of a finished solve return at
@@ -566,6 +589,8 @@ static int run_cg(fftg_handle* h, int nf, const void* tangent, long long tstride
         if (g) {
             CK(cudaMemsetAsync(h->guard, 0, sizeof(unsigned int), h->stream));
             CK(cudaGraphLaunch(g->exec, h->stream));
+            int rc = launch_cg_finish(h, nf);
+            if (rc) return rc;
             // one launch of each kernel of an iteration per loop pass
             CK(cudaMemcpyAsync(h->h_cg, h->cg, nf * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
@@ -595,7 +620,7 @@ static int run_cg(fftg_handle* h, int nf, const void* tangent, long long tstride
         CK(cudaMemcpyAsync(h->h_cg, h->cg, nf * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
     }
-    return FFTG_OK;
+    return launch_cg_finish(h, nf);
 }
 
 static void set_cg_params(fftg_handle* h, int nf, double tol, const int* run) {

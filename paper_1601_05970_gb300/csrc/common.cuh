@@ -40,7 +40,8 @@ struct CGState {
     int fixed_it;    // > 0: exactly this many iterations (set by the host)
     int done;        // CG_* status
     unsigned int ticket;  // last-block counter (always 0 between kernels)
-    int pad;
+    int pend;        // 1: x still lacks alpha p of the last update (the next
+                     // P1 or the finishing kernel adds it)
 };
 
 // Scalars of one Newton iteration / one constitutive evaluation.

@@ -29,6 +29,7 @@ struct PassArgs {
     void* out;             // P1: spectrum; P2-P4: spectrum (in place); P5: real field
     const void* aux;       // P1_CG: r; P5_DOT: p
     void* aux2;            // P1_CG: p (updated in place)
+    void* aux3;            // P1_CG: x (gets the previous iteration's alpha p)
     const void* tangent;   // [7][V]: K, 2G_eff, w11, w22, w23, w13, w12
     CGState* cg;           // per field, or null
     double* partials;      // [nf][nblocks][2]
@@ -71,6 +72,14 @@ struct PassArgs {
 #endif
 #ifndef FFTG_ROWS
 #define FFTG_ROWS 0
+#endif
+// Ghat in P3: 0 = fused into stage B in registers (lane pairs), 1 = a
+// separate phase over (column, frequency) points in shared memory. The
+// separate phase does each point once with all six components (no work
+// duplicated across a lane pair): at 243^3 it took P3 from 0.206 to 0.185 ms
+// (FP32) and from 7.4 to 6.2 ms (FP64).
+#ifndef FFTG_P3_GHAT
+#define FFTG_P3_GHAT 1
 #endif
 
 template <typename T, int W>
@@ -201,10 +210,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 1) k
     const long long cs = a.cs;
     const T* in = (const T*)a.in + f * a.fstride;
     const T* tg = (const T*)a.tangent + f * a.tstride;
-    T beta = T(0);
+    T beta = T(0), alpha = T(0);
     bool first = true;  // first CG iteration: p = r (p holds no data yet)
     if (MODE == P1_CG) {
         beta = (T)a.cg[f].beta;
+        alpha = (T)a.cg[f].alpha;
         first = a.cg[f].it == 0;
     }
     // Elementwise phase: each lane takes VW consecutive voxels of the block's
@@ -222,16 +232,24 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 1) k
             const long long v0 = base + i0;
             T p[6][VW];
             if (MODE == P1_CG) {
+                // x += alpha p (the step of the previous iteration, which the
+                // update kernel left to this pass), then p = r + beta p
                 const T* r = (const T*)a.aux + f * a.fstride;
                 T* pp = (T*)a.aux2 + f * a.fstride;
+                T* xx = (T*)a.aux3 + f * a.fstride;
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
                     ldv<VW, T>(r + c * cs + v0, p[c]);
                     if (!first) {
-                        T po[VW];
+                        T po[VW], xo[VW];
                         ldv<VW, T>(pp + c * cs + v0, po);
+                        ldv<VW, T>(xx + c * cs + v0, xo);
 #pragma unroll
-                        for (int e = 0; e < VW; ++e) p[c][e] += beta * po[e];
+                        for (int e = 0; e < VW; ++e) {
+                            xo[e] += alpha * po[e];
+                            p[c][e] += beta * po[e];
+                        }
+                        stv<VW, T>(xx + c * cs + v0, xo);
                     }
                     stv<VW, T>(pp + c * cs + v0, p[c]);
                 }
@@ -360,37 +378,36 @@ __global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
     }
 }
 
-// 1/sqrt(x): the hardware reciprocal square root in FP32 (about 2 ulp, far
-// inside the FP32 path's tolerance), correctly rounded operations in FP64.
+// 1/sqrt(x): CUDA's rsqrtf (about 2 ulp, far inside the FP32 path's
+// tolerance) and rsqrt (1 ulp) in FP64.
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
-// Ghat : tau at frequency (f1, f2, f3), times `scale`, for the 6 complex
-// components (11, 22, 33, 23, 13, 12) held at stride `cs` in shared memory.
+// Ghat : tau at frequency (f1, f2, f3), times `scale`, in place on the six
+// complex components (11, 22, 33, 23, 13, 12) held at stride `cs` in shared
+// memory. With n = xi/|xi|, t = tau n and u = t - (n.t/2) n, the closed form
+// n(x)t + t(x)n - (n.t) n(x)n equals n(x)u + u(x)n (Appendix A); at xi = 0
+// the factor 1/|xi| is taken as 0, so the mean mode maps to zero.
 template <typename T>
-__device__ __forceinline__ void apply_ghat(cplx<T>* b, int cs, int f1, int f2, int f3, T scale) {
+__device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, int f3, T scale) {
     const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(f3) * T(f3);
-    if (q2 == T(0)) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) b[c * cs] = mk(T(0), T(0));
-        return;
-    }
-    const T inv = T(1) / sqrt(q2);
+    const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
     const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(f3) * inv;
-    cplx<T> t[6];
+    cplx<T> c[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) t[c] = b[c * cs];
-    // v = tau n
-    const cplx<T> v0 = n0 * t[0] + n1 * t[5] + n2 * t[4];
-    const cplx<T> v1 = n0 * t[5] + n1 * t[1] + n2 * t[3];
-    const cplx<T> v2 = n0 * t[4] + n1 * t[3] + n2 * t[2];
-    const cplx<T> sn = n0 * v0 + n1 * v1 + n2 * v2;
-    b[0 * cs] = scale * (T(2) * n0 * v0 - (n0 * n0) * sn);
-    b[1 * cs] = scale * (T(2) * n1 * v1 - (n1 * n1) * sn);
-    b[2 * cs] = scale * (T(2) * n2 * v2 - (n2 * n2) * sn);
-    b[3 * cs] = scale * (n1 * v2 + n2 * v1 - (n1 * n2) * sn);
-    b[4 * cs] = scale * (n0 * v2 + n2 * v0 - (n0 * n2) * sn);
-    b[5 * cs] = scale * (n0 * v1 + n1 * v0 - (n0 * n1) * sn);
+    for (int k = 0; k < 6; ++k) c[k] = b[k * cs];
+    const cplx<T> t0 = n0 * c[0] + n1 * c[5] + n2 * c[4];
+    const cplx<T> t1 = n0 * c[5] + n1 * c[1] + n2 * c[3];
+    const cplx<T> t2 = n0 * c[4] + n1 * c[3] + n2 * c[2];
+    const cplx<T> h = T(-0.5) * (n0 * t0 + n1 * t1 + n2 * t2);
+    const cplx<T> u0 = t0 + n0 * h, u1 = t1 + n1 * h, u2 = t2 + n2 * h;
+    const T m0 = scale * n0, m1 = scale * n1, m2 = scale * n2;
+    b[0 * cs] = (T(2) * m0) * u0;
+    b[1 * cs] = (T(2) * m1) * u1;
+    b[2 * cs] = (T(2) * m2) * u2;
+    b[3 * cs] = m1 * u2 + m2 * u1;
+    b[4 * cs] = m0 * u2 + m2 * u0;
+    b[5 * cs] = m0 * u1 + m1 * u0;
 }
 
 // ------------------------------------------------------------- P3 (x1 + Ghat)
@@ -427,65 +444,93 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
     __syncthreads();
     const T scale = (T)a.scale;
     const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
-    // Uniform loop: every lane of every warp runs the same iterations and
-    // the shuffles; lanes without a valid item compute on zeros and store
-    // nothing.
-    for (int it0 = 0; it0 < 2 * W * N1; it0 += NT) {
-        const int it = it0 + tid;
-        const int half = it & 1, pair = it >> 1;
-        const int w = pair % W, k1 = (pair / W) % N1, col = col0 + w;
-        const bool valid = (it < 2 * W * N1) && (col < H);
-        cplx<T> v[3][N2];
-        cplx<T>* b = buf + (3 * half) * N * W + w;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-            for (int q = 0; q < N2; ++q)
-                v[c][q] = valid ? b[c * N * W + (N2 * k1 + q) * W] : mk(T(0), T(0));
-            if (N2 > 1) RegDFT<N, N2, -1, T>::run(v[c], tw);
+    if constexpr (FFTG_P3_GHAT == 1) {
+        // Separate middle phases: stage B forward in place (permuted order),
+        // Ghat with one thread per (column, frequency) holding all six
+        // components, stage B inverse in place.
+        if (N2 > 1) {
+            for (int it = tid; it < P * N1; it += NT) {
+                const int pc = it % P, k1 = it / P;
+                const int c = pc / W, w = pc - c * W;
+                if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+            }
+            __syncthreads();
         }
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-            const int kk = k1 + N1 * k2;
-            const int f1 = (kk <= (N - 1) / 2) ? kk : kk - N;
-            const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(col) * T(col);
-            const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
-            const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(col) * inv;
-            // Branch-free across the lane pair. Lane 0 holds (11, 22, 33),
-            // lane 1 (23, 13, 12); with A = diag(n) on lane 0 and
-            // A = [[0, n2, n1], [n2, 0, n0], [n1, n0, 0]] on lane 1, each lane's
-            // share of tau n is u = A v; t = u0 + u1 (shuffle) is tau n,
-            // s = n . t, and the lane's outputs are w A t - D s with w = 2,
-            // D = (n0^2, n1^2, n2^2) on lane 0 and w = 1, D = (n1 n2, n0 n2,
-            // n0 n1) on lane 1 (the closed form n(x)t + t(x)n - s n(x)n).
-            const bool sh = half != 0;
-            const T a00 = sh ? T(0) : n0, a01 = sh ? n2 : T(0), a02 = sh ? n1 : T(0);
-            const T a10 = sh ? n2 : T(0), a11 = sh ? T(0) : n1, a12 = sh ? n0 : T(0);
-            const T a20 = sh ? n1 : T(0), a21 = sh ? n0 : T(0), a22 = sh ? T(0) : n2;
-            const cplx<T> u0 = a00 * v[0][k2] + a01 * v[1][k2] + a02 * v[2][k2];
-            const cplx<T> u1 = a10 * v[0][k2] + a11 * v[1][k2] + a12 * v[2][k2];
-            const cplx<T> u2 = a20 * v[0][k2] + a21 * v[1][k2] + a22 * v[2][k2];
-            const cplx<T> t0 = u0 + mk(__shfl_xor_sync(0xffffffffu, u0.x, 1), __shfl_xor_sync(0xffffffffu, u0.y, 1));
-            const cplx<T> t1 = u1 + mk(__shfl_xor_sync(0xffffffffu, u1.x, 1), __shfl_xor_sync(0xffffffffu, u1.y, 1));
-            const cplx<T> t2 = u2 + mk(__shfl_xor_sync(0xffffffffu, u2.x, 1), __shfl_xor_sync(0xffffffffu, u2.y, 1));
-            const cplx<T> sn = n0 * t0 + n1 * t1 + n2 * t2;  // n . tau n
-            const T w = (sh ? T(1) : T(2)) * scale;
-            const T d0 = scale * (sh ? n1 * n2 : n0 * n0);
-            const T d1 = scale * (sh ? n0 * n2 : n1 * n1);
-            const T d2 = scale * (sh ? n0 * n1 : n2 * n2);
-            v[0][k2] = w * (a00 * t0 + a01 * t1 + a02 * t2) - d0 * sn;
-            v[1][k2] = w * (a10 * t0 + a11 * t1 + a12 * t2) - d1 * sn;
-            v[2][k2] = w * (a20 * t0 + a21 * t1 + a22 * t2) - d2 * sn;
+        for (int it = tid; it < W * N; it += NT) {
+            const int w = it % W, pos = it / W, col = col0 + w;
+            const int k1 = pos / N2, k2 = pos - k1 * N2;
+            const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
+            if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
         }
-        if (valid) {
+        __syncthreads();
+        if (N2 > 1) {
+            for (int it = tid; it < P * N1; it += NT) {
+                const int pc = it % P, k1 = it / P;
+                const int c = pc / W, w = pc - c * W;
+                if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+            }
+        }
+    } else {
+        // Uniform loop: every lane of every warp runs the same iterations and
+        // the shuffles; lanes without a valid item compute on zeros and store
+        // nothing.
+        for (int it0 = 0; it0 < 2 * W * N1; it0 += NT) {
+            const int it = it0 + tid;
+            const int half = it & 1, pair = it >> 1;
+            const int w = pair % W, k1 = (pair / W) % N1, col = col0 + w;
+            const bool valid = (it < 2 * W * N1) && (col < H);
+            cplx<T> v[3][N2];
+            cplx<T>* b = buf + (3 * half) * N * W + w;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (N2 > 1) RegDFT<N, N2, +1, T>::run(v[c], tw);
 #pragma unroll
-                for (int t = 0; t < N2; ++t) {
-                    cplx<T> z = v[c][t];
-                    if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[t * k1]);  // t*k1 < N
-                    b[c * N * W + (N2 * k1 + t) * W] = z;
+                for (int q = 0; q < N2; ++q)
+                    v[c][q] = valid ? b[c * N * W + (N2 * k1 + q) * W] : mk(T(0), T(0));
+                if (N2 > 1) RegDFT<N, N2, -1, T>::run(v[c], tw);
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int kk = k1 + N1 * k2;
+                const int f1 = (kk <= (N - 1) / 2) ? kk : kk - N;
+                const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(col) * T(col);
+                const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
+                const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(col) * inv;
+                // Branch-free across the lane pair. Lane 0 holds (11, 22, 33),
+                // lane 1 (23, 13, 12); with A = diag(n) on lane 0 and
+                // A = [[0, n2, n1], [n2, 0, n0], [n1, n0, 0]] on lane 1, each lane's
+                // share of tau n is u = A v; t = u0 + u1 (shuffle) is tau n,
+                // s = n . t, and the lane's outputs are w A t - D s with w = 2,
+                // D = (n0^2, n1^2, n2^2) on lane 0 and w = 1, D = (n1 n2, n0 n2,
+                // n0 n1) on lane 1 (the closed form n(x)t + t(x)n - s n(x)n).
+                const bool sh = half != 0;
+                const T a00 = sh ? T(0) : n0, a01 = sh ? n2 : T(0), a02 = sh ? n1 : T(0);
+                const T a10 = sh ? n2 : T(0), a11 = sh ? T(0) : n1, a12 = sh ? n0 : T(0);
+                const T a20 = sh ? n1 : T(0), a21 = sh ? n0 : T(0), a22 = sh ? T(0) : n2;
+                const cplx<T> u0 = a00 * v[0][k2] + a01 * v[1][k2] + a02 * v[2][k2];
+                const cplx<T> u1 = a10 * v[0][k2] + a11 * v[1][k2] + a12 * v[2][k2];
+                const cplx<T> u2 = a20 * v[0][k2] + a21 * v[1][k2] + a22 * v[2][k2];
+                const cplx<T> t0 = u0 + mk(__shfl_xor_sync(0xffffffffu, u0.x, 1), __shfl_xor_sync(0xffffffffu, u0.y, 1));
+                const cplx<T> t1 = u1 + mk(__shfl_xor_sync(0xffffffffu, u1.x, 1), __shfl_xor_sync(0xffffffffu, u1.y, 1));
+                const cplx<T> t2 = u2 + mk(__shfl_xor_sync(0xffffffffu, u2.x, 1), __shfl_xor_sync(0xffffffffu, u2.y, 1));
+                const cplx<T> sn = n0 * t0 + n1 * t1 + n2 * t2;  // n . tau n
+                const T w = (sh ? T(1) : T(2)) * scale;
+                const T d0 = scale * (sh ? n1 * n2 : n0 * n0);
+                const T d1 = scale * (sh ? n0 * n2 : n1 * n1);
+                const T d2 = scale * (sh ? n0 * n1 : n2 * n2);
+                v[0][k2] = w * (a00 * t0 + a01 * t1 + a02 * t2) - d0 * sn;
+                v[1][k2] = w * (a10 * t0 + a11 * t1 + a12 * t2) - d1 * sn;
+                v[2][k2] = w * (a20 * t0 + a21 * t1 + a22 * t2) - d2 * sn;
+            }
+            if (valid) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (N2 > 1) RegDFT<N, N2, +1, T>::run(v[c], tw);
+#pragma unroll
+                    for (int t = 0; t < N2; ++t) {
+                        cplx<T> z = v[c][t];
+                        if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[t * k1]);  // t*k1 < N
+                        b[c * N * W + (N2 * k1 + t) * W] = z;
+                    }
                 }
             }
         }
@@ -614,6 +659,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 1) k
     if (MODE == P5_DOT) {
         const double pq = tot[0];
         cg->pq = pq;
+        cg->pend = 0;  // P1 of this iteration has added the previous step
         if (!isfinite(pq)) {
             cg->done = CG_BREAKDOWN;
         } else if (!(pq > 0.0)) {

@@ -92,35 +92,42 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
         }
         const double eb = epbar[v];
         const double tr = e[0] + e[1] + e[2];
-        const double m = tr / 3.0;
+        const double m = tr * (1.0 / 3.0);
+        const double g2e = 2.0 * G;
         double s[6];
-        s[0] = 2.0 * G * (e[0] - m);
-        s[1] = 2.0 * G * (e[1] - m);
-        s[2] = 2.0 * G * (e[2] - m);
-        s[3] = 2.0 * G * e[3];
-        s[4] = 2.0 * G * e[4];
-        s[5] = 2.0 * G * e[5];
+        s[0] = g2e * (e[0] - m);
+        s[1] = g2e * (e[1] - m);
+        s[2] = g2e * (e[2] - m);
+        s[3] = g2e * e[3];
+        s[4] = g2e * e[4];
+        s[5] = g2e * e[5];
         const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
                           2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
         const double seq = sqrt(1.5 * ss);
         const double phi = seq - (sy + Hh * eb);
         double sig[6];
-        double g2 = 2.0 * G;
+        double g2 = g2e;
         double w[6] = {0, 0, 0, 0, 0, 0};
         double dg = 0.0;
         if (phi > a.tie * sy) {
-            dg = phi / (3.0 * G + Hh);
-            const double f = 1.5 / seq;
+            // one division gives both 1/sigma_eq and 1/(3G + H)
+            const double h3 = 3.0 * G + Hh;
+            const double rr = 1.0 / (seq * h3);
+            const double inv_seq = rr * h3, inv_h3 = rr * seq;
+            dg = phi * inv_h3;
+            const double f = 1.5 * inv_seq;
+            const double gdg = g2e * dg;
             double Nn[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                sig[c] = s[c] - 2.0 * G * dg * Nn[c];
+                sig[c] = s[c] - gdg * Nn[c];
                 ep[c] += dg * Nn[c];
             }
-            g2 = 2.0 * G - 6.0 * G * G * dg / seq;
-            const double b = 4.0 * G * G * (dg / seq - 1.0 / (3.0 * G + Hh));
+            const double dgs = dg * inv_seq;
+            g2 = g2e - 6.0 * G * G * dgs;
+            const double b = 4.0 * G * G * (dgs - inv_h3);
             const double sb = sqrt(fmax(-b, 0.0));
 #pragma unroll
             for (int c = 0; c < 6; ++c) w[c] = sb * Nn[c];
@@ -185,7 +192,10 @@ struct VecArgs {
     long long cell_fields;  // stride between cells of eps (newton update)
 };
 
-// x += alpha p; r -= alpha q; rr = <r, r>; then beta, stopping test.
+// r -= alpha q; rr = <r, r>; then beta, stopping test. The matching step
+// x += alpha p is deferred: the next iteration's P1 adds it while it reads
+// p anyway, and k_cg_finish adds the last one (CGState::pend), so x costs
+// no extra pass over memory.
 // 16-byte vectors over the padded components; lanes in the padding are
 // updated too (harmless) but left out of <r, r>.
 template <typename T>
@@ -198,9 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
     const long long V = a.V, cs = a.cs;
     const long long nv = cs / VW;
     const T alpha = (T)cg->alpha;
-    VT* x = (VT*)((T*)a.x + f * a.fstride);
     VT* r = (VT*)((T*)a.r + f * a.fstride);
-    const VT* p = (const VT*)((const T*)a.p + f * a.fstride);
     const VT* q = (const VT*)((const T*)a.q + f * a.fstride);
     T acc = T(0);
     for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < nv;
@@ -208,21 +216,15 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
         T rv[6][VW];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            VT xv = x[c * nv + j];
-            const VT pv = p[c * nv + j];
             VT rr = r[c * nv + j];
             const VT qv = q[c * nv + j];
-            T* xe = reinterpret_cast<T*>(&xv);
             T* re = reinterpret_cast<T*>(&rr);
-            const T* pe = reinterpret_cast<const T*>(&pv);
             const T* qe = reinterpret_cast<const T*>(&qv);
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                xe[e] += alpha * pe[e];
                 re[e] -= alpha * qe[e];
                 rv[c][e] = re[e];
             }
-            x[c * nv + j] = xv;
             r[c * nv + j] = rr;
         }
 #pragma unroll
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
     const double rr = tot[0];
     const int it = cg->it + 1;
     cg->it = it;
+    cg->pend = 1;
     cg->beta = rr / cg->rr;
     cg->rr = rr;
     if (!isfinite(rr)) {
@@ -259,6 +262,31 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
         } else if (it - cg->it_min >= cg->stag_window) {
             cg->done = CG_STAGNATED;
         }
+    }
+}
+
+// After the last CG iteration: x += alpha p where the last update left the
+// step pending.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cg_finish(VecArgs a) {
+    const int f = blockIdx.z;
+    const CGState* cg = a.cg + f;
+    if (!cg->pend) return;
+    constexpr int VW = 16 / (int)sizeof(T);
+    using VT = typename Vec16<T>::type;
+    const long long nv = 6 * a.cs / VW;
+    const T alpha = (T)cg->alpha;
+    VT* x = (VT*)((T*)a.x + f * a.fstride);
+    const VT* p = (const VT*)((const T*)a.p + f * a.fstride);
+    for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < nv;
+         j += (long long)gridDim.x * kThreads) {
+        VT xv = x[j];
+        const VT pv = p[j];
+        T* xe = reinterpret_cast<T*>(&xv);
+        const T* pe = reinterpret_cast<const T*>(&pv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) xe[e] += alpha * pe[e];
+        x[j] = xv;
     }
 }
 
@@ -290,42 +318,35 @@ __global__ void __launch_bounds__(kThreads) k_newton_update(VecArgs a) {
     if (threadIdx.x == 0) nd->de2 = tot[0];
 }
 
+// s = C : p at voxel v with the compact tangent in the tangent's precision
 template <typename T>
 __device__ __forceinline__ void tangent_apply_v(const T* __restrict__ tg, long long v, long long cs,
-                                                const double (&p)[6], double (&s)[6]) {
-    const double K = tg[v], g2 = tg[cs + v];
-    const double w0 = tg[2 * cs + v], w1 = tg[3 * cs + v], w3 = tg[4 * cs + v], w4 = tg[5 * cs + v],
-                 w5 = tg[6 * cs + v];
-    const double w2 = -(w0 + w1);
-    const double tr = p[0] + p[1] + p[2], m = tr / 3.0;
-    const double wp = w0 * p[0] + w1 * p[1] + w2 * p[2] + 2.0 * (w3 * p[3] + w4 * p[4] + w5 * p[5]);
-    s[0] = K * tr + g2 * (p[0] - m) - wp * w0;
-    s[1] = K * tr + g2 * (p[1] - m) - wp * w1;
-    s[2] = K * tr + g2 * (p[2] - m) - wp * w2;
-    s[3] = g2 * p[3] - wp * w3;
-    s[4] = g2 * p[4] - wp * w4;
-    s[5] = g2 * p[5] - wp * w5;
+                                                const T (&p)[6], T (&s)[6]) {
+    apply_tangent7<T>(tg[v], tg[cs + v], tg[2 * cs + v], tg[3 * cs + v], tg[4 * cs + v],
+                      tg[5 * cs + v], tg[6 * cs + v], p, s);
 }
 
 // Roundoff floors of the six tangent right-hand sides: ||C : E_j||^2.
+// Products in the tangent's precision, per-thread sums in T, block sums and
+// the total in FP64 (only the order of magnitude matters for a floor).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_tangent_floor(VecArgs a) {
     const long long V = a.V;
     const T* tg = (const T*)a.tangent;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    T acc[6] = {0, 0, 0, 0, 0, 0};
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
          v += (long long)gridDim.x * kThreads) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            double e[6] = {0, 0, 0, 0, 0, 0}, s[6];
-            e[j] = 1.0;
+            T e[6] = {0, 0, 0, 0, 0, 0}, s[6];
+            e[j] = T(1);
             tangent_apply_v<T>(tg, v, a.cs, e, s);
-            acc[j] += frob<double>(s, s);
+            acc[j] += frob<T>(s, s);
         }
     }
     double part[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) part[j] = block_sum(acc[j]);
+    for (int j = 0; j < 6; ++j) part[j] = block_sum((double)acc[j]);
     if (!publish_partials<6>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
     double tot[6];
     reduce_partials<6>(a.partials, gridDim.x, &a.nd->ticket, tot);
@@ -333,22 +354,25 @@ __global__ void __launch_bounds__(kThreads) k_tangent_floor(VecArgs a) {
         for (int j = 0; j < 6; ++j) a.cg[j].floor2 = kRoundoffRel * kRoundoffRel * tot[j];
 }
 
-// out[i*6 + j] = sum over voxels of (C : (E_j + x_j))_i
+// out[i*6 + j] = sum over voxels of (C : (E_j + x_j))_i. C : (E_j + x_j) is
+// formed in the precision of the tangent and of x (FP32 in the mixed path,
+// where both are FP32); each thread sums its few voxels in that precision
+// and the block and grid sums are FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_tangent_average(VecArgs a) {
     const long long V = a.V;
     const T* tg = (const T*)a.tangent;
     const T* x = (const T*)a.x;
-    double acc[36];
+    T acc[36];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 36; ++k) acc[k] = T(0);
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
          v += (long long)gridDim.x * kThreads) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            double e[6], s[6];
+            T e[6], s[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) e[c] = (double)x[j * a.fstride + c * a.cs + v] + (c == j ? 1.0 : 0.0);
+            for (int c = 0; c < 6; ++c) e[c] = x[j * a.fstride + c * a.cs + v] + (c == j ? T(1) : T(0));
             tangent_apply_v<T>(tg, v, a.cs, e, s);
 #pragma unroll
             for (int i = 0; i < 6; ++i) acc[i * 6 + j] += s[i];
@@ -356,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_average(VecArgs a) {
     }
     double part[36];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) part[k] = block_sum(acc[k]);
+    for (int k = 0; k < 36; ++k) part[k] = block_sum((double)acc[k]);
     if (!publish_partials<36>(part, a.partials, blockIdx.x, gridDim.x, &a.nd->ticket)) return;
     double tot[36];
     reduce_partials<36>(a.partials, gridDim.x, &a.nd->ticket, tot);
