@@ -63,6 +63,16 @@ struct PassArgs {
 #ifndef FFTG_P5_MINB
 #define FFTG_P5_MINB 4
 #endif
+// P5: rounds of spectrum loads (LDB) and of p loads (PB) issued together,
+// so that more loads are in flight per thread: at 243^3 LDB = 4, PB = 2
+// took P5 from 0.177 to 0.157 ms (PB = 4 or one voxel per lane: no further
+// gain; 3 blocks per SM instead of 4: 0.173 ms).
+#ifndef FFTG_P5_LDB
+#define FFTG_P5_LDB 4
+#endif
+#ifndef FFTG_P5_PB
+#define FFTG_P5_PB 2
+#endif
 
 // Block shapes: P3 columns per block (0 = as many as fit ~100 KB of shared
 // memory, at most 32) and P1/P5 rows per block (0 = as many as fit ~50 KB,
@@ -191,7 +201,7 @@ struct Vec16<double> {
 
 // ----------------------------------------------------------------------- P1
 template <int N, typename T, int MODE>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 1) k_p1(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 2) k_p1(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
 // T: FFT precision; TO: output real type (P5_RHS writes the CG residual r
 // in the inner precision).
 template <int N, typename T, int MODE, typename TO>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 1) k_p5(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 2) k_p5(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -566,16 +576,40 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 1) k
     const int nel = nrows * N;
     const cplx<T>* in = (const cplx<T>*)a.in + f * a.sstride;
     const long long HS = (long long)N * N * H;
-    for (int it = tid; it < nrows * H; it += kThreads) {
-        const int row = it / H, k = it - row * H;
-        const long long o = (long long)(row0 + row) * H + k;
-        const int pk = perm_pos<N>(k);
-        const int pn = perm_pos<N>(k == 0 ? 0 : N - k);
+    // Spectrum rows -> tile: the loads of FFTG_P5_LDB rounds are issued
+    // before their stores, so that more of them are in flight.
+    constexpr int NRL = (R * H + kThreads - 1) / kThreads;
+    constexpr int LB = FFTG_P5_LDB < NRL ? FFTG_P5_LDB : NRL;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const cplx<T> A = in[(2 * c) * HS + o], B = in[(2 * c + 1) * HS + o];
-            z[(c * R + row) * N + pk] = mk(A.x - B.y, A.y + B.x);  // A + iB
-            if (k > 0) z[(c * R + row) * N + pn] = mk(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+    for (int r0 = 0; r0 < NRL; r0 += LB) {
+        cplx<T> A[LB][3], B[LB][3];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int it = tid + (r0 + u) * kThreads;
+            if (r0 + u < NRL && it < nrows * H) {
+                const int row = it / H, k = it - row * H;
+                const long long o = (long long)(row0 + row) * H + k;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    A[u][c] = in[(2 * c) * HS + o];
+                    B[u][c] = in[(2 * c + 1) * HS + o];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int it = tid + (r0 + u) * kThreads;
+            if (r0 + u < NRL && it < nrows * H) {
+                const int row = it / H, k = it - row * H;
+                const int pk = perm_pos<N>(k);
+                const int pn = perm_pos<N>(k == 0 ? 0 : N - k);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const cplx<T> a0 = A[u][c], b0 = B[u][c];
+                    z[(c * R + row) * N + pk] = mk(a0.x - b0.y, a0.y + b0.x);  // A + iB
+                    if (k > 0) z[(c * R + row) * N + pn] = mk(a0.x + b0.y, b0.x - a0.y);  // conj(A) + i conj(B)
+                }
+            }
         }
     }
     __syncthreads();
@@ -601,47 +635,64 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 1) k
     // conflicts. Lanes past the grid in the last block write only component
     // padding and are left out of the sums.
     constexpr int VO = (FFTG_P5_VW * (int)sizeof(TO) > 16) ? 16 / (int)sizeof(TO) : FFTG_P5_VW;
-    for (int j = tid; j < (R * N) / VO; j += kThreads) {
-        const int i0 = j * VO;
-        if (i0 >= nel) continue;
-        const long long v0 = base + i0;
-        TO q[6][VO];
-        T qd[6][VO];
+    // FFTG_P5_PB rounds at a time: the loads of p for all of them first.
+    constexpr int NV = (R * N) / VO;
+    constexpr int NRE = (NV + kThreads - 1) / kThreads;
+    constexpr int PB = FFTG_P5_PB < NRE ? FFTG_P5_PB : NRE;
+    const TO* pin = (const TO*)a.aux + f * a.fstride;
 #pragma unroll
-        for (int e = 0; e < VO; ++e) {
-            const cplx<T> z0 = z[i0 + e], z1 = z[R * N + i0 + e], z2 = z[2 * R * N + i0 + e];
-            qd[0][e] = z0.x;
-            qd[1][e] = z0.y;
-            qd[2][e] = z1.x;
-            qd[3][e] = z1.y;
-            qd[4][e] = z2.x;
-            qd[5][e] = z2.y;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) q[c][e] = (TO)qd[c][e];
-        }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) stv<VO, TO>(out + c * cs + v0, q[c]);
+    for (int r0 = 0; r0 < NRE; r0 += PB) {
+        TO pv[PB][6][VO];
         if (MODE == P5_DOT) {
-            const TO* p = (const TO*)a.aux + f * a.fstride;
-            TO pv[6][VO];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) ldv<VO, TO>(p + c * cs + v0, pv[c]);
+            for (int u = 0; u < PB; ++u) {
+                const int j = tid + (r0 + u) * kThreads;
+                if (r0 + u < NRE && j < NV && j * VO < nel) {
 #pragma unroll
-            for (int e = 0; e < VO; ++e) {
-                if (i0 + e < nel) {
-                    const TO pe[6] = {pv[0][e], pv[1][e], pv[2][e], pv[3][e], pv[4][e], pv[5][e]};
-                    const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
-                    acc0 += (T)frob<TO>(pe, qe);
+                    for (int c = 0; c < 6; ++c) ldv<VO, TO>(pin + c * cs + base + j * VO, pv[u][c]);
                 }
             }
-        } else if (MODE == P5_RHS) {
+        }
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            const int j = tid + (r0 + u) * kThreads;
+            const int i0 = j * VO;
+            if (!(r0 + u < NRE && j < NV && i0 < nel)) continue;
+            const long long v0 = base + i0;
+            TO q[6][VO];
+            T qd[6][VO];
 #pragma unroll
             for (int e = 0; e < VO; ++e) {
-                if (i0 + e < nel) {
-                    const T qde[6] = {qd[0][e], qd[1][e], qd[2][e], qd[3][e], qd[4][e], qd[5][e]};
-                    const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
-                    acc1 += (double)frob<T>(qde, qde);
-                    acc0 += (T)frob<TO>(qe, qe);
+                const cplx<T> z0 = z[i0 + e], z1 = z[R * N + i0 + e], z2 = z[2 * R * N + i0 + e];
+                qd[0][e] = z0.x;
+                qd[1][e] = z0.y;
+                qd[2][e] = z1.x;
+                qd[3][e] = z1.y;
+                qd[4][e] = z2.x;
+                qd[5][e] = z2.y;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) q[c][e] = (TO)qd[c][e];
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) stv<VO, TO>(out + c * cs + v0, q[c]);
+            if (MODE == P5_DOT) {
+#pragma unroll
+                for (int e = 0; e < VO; ++e) {
+                    if (i0 + e < nel) {
+                        const TO pe[6] = {pv[u][0][e], pv[u][1][e], pv[u][2][e], pv[u][3][e], pv[u][4][e], pv[u][5][e]};
+                        const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
+                        acc0 += (T)frob<TO>(pe, qe);
+                    }
+                }
+            } else if (MODE == P5_RHS) {
+#pragma unroll
+                for (int e = 0; e < VO; ++e) {
+                    if (i0 + e < nel) {
+                        const T qde[6] = {qd[0][e], qd[1][e], qd[2][e], qd[3][e], qd[4][e], qd[5][e]};
+                        const TO qe[6] = {q[0][e], q[1][e], q[2][e], q[3][e], q[4][e], q[5][e]};
+                        acc1 += (double)frob<T>(qde, qde);
+                        acc0 += (T)frob<TO>(qe, qe);
+                    }
                 }
             }
         }

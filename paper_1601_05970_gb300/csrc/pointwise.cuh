@@ -59,8 +59,10 @@ struct ConstArgs {
 // eps_p += dgamma N, epbar += dgamma, sigma -= 2G dgamma N, and the tangent
 // C = C_e - 6G^2 dgamma/sigma_eq I_d + 4G^2 (dgamma/sigma_eq - 1/(3G+H)) N(x)N
 // stored as K, 2G_eff, w = sqrt(-b) N (b the N(x)N coefficient, negative).
+// Two blocks per SM (at most 128 registers): unbounded, the kernel takes
+// about 155 registers and runs one block per SM, 5 % slower at 243^3.
 template <typename TT>
-__global__ void __launch_bounds__(kThreads) k_constitutive(ConstArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
     const int cell = blockIdx.y;
     if (a.active && !a.active[cell]) return;
     const long long V = a.V, cs = a.cs;
