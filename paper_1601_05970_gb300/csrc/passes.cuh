@@ -74,6 +74,10 @@ struct PassArgs {
 #define FFTG_P5_PB 2
 #endif
 
+#ifndef FFTG_P3_TB
+#define FFTG_P3_TB 1
+#endif
+
 // Block shapes: P3 columns per block (0 = as many as fit ~100 KB of shared
 // memory, at most 32) and P1/P5 rows per block (0 = as many as fit ~50 KB,
 // at least 4).
@@ -82,14 +86,6 @@ struct PassArgs {
 #endif
 #ifndef FFTG_ROWS
 #define FFTG_ROWS 0
-#endif
-// Ghat in P3: 0 = fused into stage B in registers (lane pairs), 1 = a
-// separate phase over (column, frequency) points in shared memory. The
-// separate phase does each point once with all six components (no work
-// duplicated across a lane pair): at 243^3 it took P3 from 0.206 to 0.185 ms
-// (FP32) and from 7.4 to 6.2 ms (FP64).
-#ifndef FFTG_P3_GHAT
-#define FFTG_P3_GHAT 1
 #endif
 
 template <typename T, int W>
@@ -152,11 +148,11 @@ struct Cfg {
     static constexpr int cap(int x) { return x > 1024 ? 1024 : x; }
     // threads of the column passes: one stage-A item per thread
     static constexpr int T2 = cap(rup32(S2 * W2 * Plan<N>::N2));
-    // P3: one stage-A item per thread, and at least two per (column, k1)
-    // pair in the fused middle stage
+    // P3: one stage-A item per thread, and (FFTG_P3_TB) at least 2*W*N1
+    // threads (448 at 243^3 rather than 432: the configuration measured)
     static constexpr int T3a = rup32(6 * W3 * Plan<N>::N2);
-    static constexpr int T3b = rup32(2 * W3 * Plan<N>::N1);
-    // single-stage plans (N2 = 1) loop over the middle stage with 256 threads
+    static constexpr int T3b = FFTG_P3_TB ? rup32(2 * W3 * Plan<N>::N1) : 0;
+    // single-stage plans (N2 = 1) loop over the middle stages with 256 threads
     static constexpr int T3 = Plan<N>::N2 == 1 ? (T3a > 256 ? cap(T3a) : 256) : cap(T3a > T3b ? T3a : T3b);
     static constexpr size_t smem_rows = (size_t)(3 * R * N + N) * CS;
     static constexpr size_t smem_p3 = (size_t)(6 * W3 * N + N) * CS;
@@ -421,12 +417,13 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
 }
 
 // ------------------------------------------------------------- P3 (x1 + Ghat)
-// Stage A forward (global -> shared), then one fused register stage per
-// (column, k1): the N2-point forward DFT of the six components, Ghat at the
-// N2 frequencies k1 + N1*k2, the N2-point inverse DFT and its twiddle, back
-// in place; then stage A inverse (shared -> global). Two adjacent lanes share
-// a (column, k1): lane 0 holds the normal components (11, 22, 33), lane 1
-// the shear ones (23, 13, 12); they exchange their parts of tau n by shuffle.
+// Stage A forward (global -> shared), stage B forward in place, Ghat with
+// one thread per (column, frequency) holding all six components, stage B
+// inverse in place, stage A inverse (shared -> global). Ghat as its own
+// phase does each point once; fusing it into stage B's registers with the
+// six components split over a lane pair duplicated n . tau n and needed
+// shuffles (at 243^3 the separate phase took P3 from 0.206 to 0.185 ms in
+// FP32 and from 7.4 to 6.2 ms in FP64).
 template <int N, typename T>
 __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T3 <= 512)
                                                       ? (Cfg<N, T>::T3 <= 256 ? 4 : 2) : 1) k_p3(PassArgs a) {
@@ -454,95 +451,29 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
     __syncthreads();
     const T scale = (T)a.scale;
     const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
-    if constexpr (FFTG_P3_GHAT == 1) {
-        // Separate middle phases: stage B forward in place (permuted order),
-        // Ghat with one thread per (column, frequency) holding all six
-        // components, stage B inverse in place.
-        if (N2 > 1) {
-            for (int it = tid; it < P * N1; it += NT) {
-                const int pc = it % P, k1 = it / P;
-                const int c = pc / W, w = pc - c * W;
-                if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
-            }
-            __syncthreads();
-        }
-        for (int it = tid; it < W * N; it += NT) {
-            const int w = it % W, pos = it / W, col = col0 + w;
-            const int k1 = pos / N2, k2 = pos - k1 * N2;
-            const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
-            if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
+    // Separate middle phases: stage B forward in place (permuted order),
+    // Ghat with one thread per (column, frequency) holding all six
+    // components, stage B inverse in place.
+    if (N2 > 1) {
+        for (int it = tid; it < P * N1; it += NT) {
+            const int pc = it % P, k1 = it / P;
+            const int c = pc / W, w = pc - c * W;
+            if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
         }
         __syncthreads();
-        if (N2 > 1) {
-            for (int it = tid; it < P * N1; it += NT) {
-                const int pc = it % P, k1 = it / P;
-                const int c = pc / W, w = pc - c * W;
-                if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
-            }
-        }
-    } else {
-        // Uniform loop: every lane of every warp runs the same iterations and
-        // the shuffles; lanes without a valid item compute on zeros and store
-        // nothing.
-        for (int it0 = 0; it0 < 2 * W * N1; it0 += NT) {
-            const int it = it0 + tid;
-            const int half = it & 1, pair = it >> 1;
-            const int w = pair % W, k1 = (pair / W) % N1, col = col0 + w;
-            const bool valid = (it < 2 * W * N1) && (col < H);
-            cplx<T> v[3][N2];
-            cplx<T>* b = buf + (3 * half) * N * W + w;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                for (int q = 0; q < N2; ++q)
-                    v[c][q] = valid ? b[c * N * W + (N2 * k1 + q) * W] : mk(T(0), T(0));
-                if (N2 > 1) RegDFT<N, N2, -1, T>::run(v[c], tw);
-            }
-#pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) {
-                const int kk = k1 + N1 * k2;
-                const int f1 = (kk <= (N - 1) / 2) ? kk : kk - N;
-                const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(col) * T(col);
-                const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
-                const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(col) * inv;
-                // Branch-free across the lane pair. Lane 0 holds (11, 22, 33),
-                // lane 1 (23, 13, 12); with A = diag(n) on lane 0 and
-                // A = [[0, n2, n1], [n2, 0, n0], [n1, n0, 0]] on lane 1, each lane's
-                // share of tau n is u = A v; t = u0 + u1 (shuffle) is tau n,
-                // s = n . t, and the lane's outputs are w A t - D s with w = 2,
-                // D = (n0^2, n1^2, n2^2) on lane 0 and w = 1, D = (n1 n2, n0 n2,
-                // n0 n1) on lane 1 (the closed form n(x)t + t(x)n - s n(x)n).
-                const bool sh = half != 0;
-                const T a00 = sh ? T(0) : n0, a01 = sh ? n2 : T(0), a02 = sh ? n1 : T(0);
-                const T a10 = sh ? n2 : T(0), a11 = sh ? T(0) : n1, a12 = sh ? n0 : T(0);
-                const T a20 = sh ? n1 : T(0), a21 = sh ? n0 : T(0), a22 = sh ? T(0) : n2;
-                const cplx<T> u0 = a00 * v[0][k2] + a01 * v[1][k2] + a02 * v[2][k2];
-                const cplx<T> u1 = a10 * v[0][k2] + a11 * v[1][k2] + a12 * v[2][k2];
-                const cplx<T> u2 = a20 * v[0][k2] + a21 * v[1][k2] + a22 * v[2][k2];
-                const cplx<T> t0 = u0 + mk(__shfl_xor_sync(0xffffffffu, u0.x, 1), __shfl_xor_sync(0xffffffffu, u0.y, 1));
-                const cplx<T> t1 = u1 + mk(__shfl_xor_sync(0xffffffffu, u1.x, 1), __shfl_xor_sync(0xffffffffu, u1.y, 1));
-                const cplx<T> t2 = u2 + mk(__shfl_xor_sync(0xffffffffu, u2.x, 1), __shfl_xor_sync(0xffffffffu, u2.y, 1));
-                const cplx<T> sn = n0 * t0 + n1 * t1 + n2 * t2;  // n . tau n
-                const T w = (sh ? T(1) : T(2)) * scale;
-                const T d0 = scale * (sh ? n1 * n2 : n0 * n0);
-                const T d1 = scale * (sh ? n0 * n2 : n1 * n1);
-                const T d2 = scale * (sh ? n0 * n1 : n2 * n2);
-                v[0][k2] = w * (a00 * t0 + a01 * t1 + a02 * t2) - d0 * sn;
-                v[1][k2] = w * (a10 * t0 + a11 * t1 + a12 * t2) - d1 * sn;
-                v[2][k2] = w * (a20 * t0 + a21 * t1 + a22 * t2) - d2 * sn;
-            }
-            if (valid) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (N2 > 1) RegDFT<N, N2, +1, T>::run(v[c], tw);
-#pragma unroll
-                    for (int t = 0; t < N2; ++t) {
-                        cplx<T> z = v[c][t];
-                        if (k1 > 0 && t > 0) z = twmul<+1>(z, tw[t * k1]);  // t*k1 < N
-                        b[c * N * W + (N2 * k1 + t) * W] = z;
-                    }
-                }
-            }
+    }
+    for (int it = tid; it < W * N; it += NT) {
+        const int w = it % W, pos = it / W, col = col0 + w;
+        const int k1 = pos / N2, k2 = pos - k1 * N2;
+        const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
+        if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
+    }
+    __syncthreads();
+    if (N2 > 1) {
+        for (int it = tid; it < P * N1; it += NT) {
+            const int pc = it % P, k1 = it / P;
+            const int c = pc / W, w = pc - c * W;
+            if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
         }
     }
     __syncthreads();
