@@ -15,7 +15,9 @@ over voxels but otherwise in the order the paper states it:
                                     closed form of Appendix A, Eq. (FT_projection)
 * reference-medium Green operator . Appendix A, Eq. (Gamma_explicit), used only
                                     to pin Ghat by an independent formula
-* J2 return mapping and tangent ... Section 4.2 (n = 1: linear hardening)
+* J2 return mapping and tangent ... Section 4.2 (hardening sigma_0 + H epbar^n;
+                                    closed-form return for n = 1, a bracketed
+                                    scalar Newton for other n)
 * CG on G C de = -G sigma ......... Eq. (linear_system), Section 2.5
 * Newton increment loop ........... Algorithm 1
 * homogenised stress .............. Eq. (trapz): the mean of the nodal stress
@@ -187,7 +189,7 @@ def inner(a, b) -> float:
 
 
 # --------------------------------------------------------------------------
-# J2 elasto-plasticity with linear hardening (Section 4.2, n = 1)
+# J2 elasto-plasticity with isotropic hardening sigma_0 + H epbar^n (Section 4.2)
 # --------------------------------------------------------------------------
 @dataclass
 class J2Result:
@@ -201,24 +203,67 @@ class J2Result:
     K: np.ndarray
     G: np.ndarray
     H: np.ndarray
+    slope: np.ndarray        # [...] n H (epbar_t + dgamma)^(n-1): hardening slope
+                             # at the returned state (H for n = 1)
 
 
 def material_fields(phase, mats):
-    """Per-voxel (K, G, sigma_y, H) arrays from a phase map."""
-    tab = np.array([m.as_tuple() if hasattr(m, "as_tuple") else tuple(m)
-                    for m in mats], dtype=np.float64)
+    """Per-voxel (K, G, sigma_y, H, n) arrays from a phase map; a material
+    given as (K, G, sigma_y, H) has n = 1."""
+    rows = []
+    for m in mats:
+        t = tuple(m.as_tuple() if hasattr(m, "as_tuple") else m)
+        rows.append(t if len(t) == 5 else t + (1.0,))
+    tab = np.array(rows, dtype=np.float64)
     ph = np.asarray(phase).astype(np.int64)
-    return tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3]
+    return tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4]
 
 
-def j2_update(eps, eps_p_t, epbar_t, K, G, sy, H, tie=1e-12):
+def power_law_dgamma(seq_tr, epbar_t, G, sy, H, n, max_iter=200):
+    """Root dgamma > 0 of the scalar return equation of Section 4.2,
+        seq_tr - 3 G dgamma - sigma_0 - H (epbar_t + dgamma)^n = 0,
+    for trial states with Phi_tr > 0 (arrays of equal shape).
+
+    The left side is positive at 0 and non-positive at Phi_tr / (3G) (the
+    hardening term only grows), so the root is bracketed there; Newton steps
+    that leave the current bracket are replaced by bisection. Iterates until
+    the bracket or the step is at the last few bits.
+    """
+    seq_tr, epbar_t, G, sy, H, n = np.broadcast_arrays(
+        *(np.asarray(v, dtype=np.float64) for v in (seq_tr, epbar_t, G, sy, H, n)))
+    phi_tr = seq_tr - (sy + H * epbar_t ** n)
+    lo = np.zeros_like(seq_tr)
+    hi = phi_tr / (3.0 * G)
+    x = 0.5 * (lo + hi)
+    for _ in range(max_iter):
+        y = epbar_t + x
+        f = seq_tr - 3.0 * G * x - sy - H * y ** n
+        lo = np.where(f > 0.0, x, lo)
+        hi = np.where(f > 0.0, hi, x)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            df = -3.0 * G - n * H * np.where(y > 0.0, y ** (n - 1.0), np.inf)
+            xn = x - f / df
+        bad = ~((xn > lo) & (xn < hi)) | ~np.isfinite(xn)
+        xn = np.where(bad, 0.5 * (lo + hi), xn)
+        done = np.abs(xn - x) <= 4.0 * np.finfo(float).eps * np.maximum(np.abs(x), 1e-300)
+        x = xn
+        if np.all(done | (hi - lo <= 4.0 * np.finfo(float).eps * hi)):
+            break
+    return x
+
+
+def j2_update(eps, eps_p_t, epbar_t, K, G, sy, H, n=None, tie=1e-12):
     """Backward-Euler elastic predictor / plastic corrector.
 
-    eps, eps_p_t: [3, 3, ...]; epbar_t, K, G, sy, H: [...].
-    Trial state (Eq. model:plas:trial), elastic branch (Eq. model:plas:elas),
-    closed-form return for n = 1: dgamma = Phi_tr / (3G + H), update
-    (Eq. model:plas:corrector).
+    eps, eps_p_t: [3, 3, ...]; epbar_t, K, G, sy, H, n: [...] (n = None:
+    linear hardening, n = 1). Trial state (Eq. model:plas:trial), elastic
+    branch (Eq. model:plas:elas), plastic corrector (Eq. model:plas:corrector)
+    with dgamma from the scalar return equation: in closed form,
+    Phi_tr / (3G + H), for n = 1 and by `power_law_dgamma` otherwise.
     """
+    if n is None:
+        n = np.ones_like(np.asarray(epbar_t, dtype=np.float64))
+    n = np.broadcast_to(np.asarray(n, dtype=np.float64), np.shape(epbar_t))
     ee = eps - eps_p_t
     tr = ee[0, 0] + ee[1, 1] + ee[2, 2]
     dev = ee - tr / 3.0 * I2.reshape(3, 3, *([1] * (ee.ndim - 2)))
@@ -226,29 +271,40 @@ def j2_update(eps, eps_p_t, epbar_t, K, G, sy, H, tie=1e-12):
     s = sig_tr - (sig_tr[0, 0] + sig_tr[1, 1] + sig_tr[2, 2]) / 3.0 * \
         I2.reshape(3, 3, *([1] * (ee.ndim - 2)))
     seq = np.sqrt(1.5 * np.sum(s * s, axis=(0, 1)))
-    phi = seq - (sy + H * epbar_t)
+    phi = seq - (sy + H * epbar_t ** n)
     plastic = phi > tie * sy
     seq_safe = np.where(seq > 0.0, seq, 1.0)
     Ntr = 1.5 * s / seq_safe
-    dgamma = np.where(plastic, phi / (3.0 * G + H), 0.0)
+    linear = n == 1.0
+    dgamma = np.where(plastic & linear, phi / (3.0 * G + H), 0.0)
+    pw = plastic & ~linear
+    if np.any(pw):
+        b = np.broadcast_arrays(seq, epbar_t, G, sy, H, n)
+        dgamma = dgamma.copy()
+        dgamma[pw] = power_law_dgamma(*(v[pw] for v in b))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        y = epbar_t + dgamma
+        slope = np.where(linear, H, n * H * np.where(y > 0.0, y ** (n - 1.0), 0.0))
     eps_p = eps_p_t + dgamma * Ntr
     epbar = epbar_t + dgamma
     ee2 = eps - eps_p
     tr2 = ee2[0, 0] + ee2[1, 1] + ee2[2, 2]
     dev2 = ee2 - tr2 / 3.0 * I2.reshape(3, 3, *([1] * (ee.ndim - 2)))
     sigma = K * tr2 * I2.reshape(3, 3, *([1] * (ee.ndim - 2))) + 2.0 * G * dev2
-    return J2Result(sigma, eps_p, epbar, plastic, dgamma, seq, Ntr, K, G, H)
+    return J2Result(sigma, eps_p, epbar, plastic, dgamma, seq, Ntr, K, G, H,
+                    np.broadcast_to(slope, np.shape(epbar_t)))
 
 
 def j2_tangent(res: J2Result, sl=slice(None)):
     """Consistent tangent C_ijlm, [3, 3, 3, 3, M] for the voxels in `sl`.
 
-    Elastic: C = C_e = K I(x)I + 2G I_d. Plastic:
-    C = C_e - 6 G^2 dgamma / seq_tr I_d + 4 G^2 (dgamma / seq_tr - 1/(3G + H)) N(x)N.
+    Elastic: C = C_e = K I(x)I + 2G I_d. Plastic (Section 4.2):
+    C = C_e - 6 G^2 dgamma / seq_tr I_d
+            + 4 G^2 (dgamma / seq_tr - 1/(3G + n H (epbar_t + dgamma)^(n-1))) N(x)N.
     """
     K = res.K.reshape(-1)[sl]
     G = res.G.reshape(-1)[sl]
-    H = res.H.reshape(-1)[sl]
+    hs = res.slope.reshape(-1)[sl]
     dg = res.dgamma.reshape(-1)[sl]
     seq = res.seq_tr.reshape(-1)[sl]
     pl = res.plastic.reshape(-1)[sl]
@@ -257,7 +313,7 @@ def j2_tangent(res: J2Result, sl=slice(None)):
          + np.einsum("ijlm,v->ijlmv", I4d, 2.0 * G))
     seqs = np.where(seq > 0.0, seq, 1.0)
     a = np.where(pl, 6.0 * G * G * dg / seqs, 0.0)
-    b = np.where(pl, 4.0 * G * G * (dg / seqs - 1.0 / (3.0 * G + H)), 0.0)
+    b = np.where(pl, 4.0 * G * G * (dg / seqs - 1.0 / (3.0 * G + hs)), 0.0)
     C -= np.einsum("ijlm,v->ijlmv", I4d, a)
     C += np.einsum("ijv,lmv,v->ijlmv", Nt, Nt, b)
     return C
@@ -341,7 +397,7 @@ class State:
 
     def __post_init__(self):
         N = self.N
-        self.K, self.G, self.sy, self.H = material_fields(self.phase, self.mats)
+        self.K, self.G, self.sy, self.H, self.n = material_fields(self.phase, self.mats)
         if self.E is None:
             self.E = np.zeros((3, 3))
         if self.eps_star is None:
@@ -353,7 +409,7 @@ class State:
 
     def constitutive(self, E, eps_star):
         eps = eps_star + E[:, :, None, None, None]
-        return j2_update(eps, self.eps_p, self.epbar, self.K, self.G, self.sy, self.H)
+        return j2_update(eps, self.eps_p, self.epbar, self.K, self.G, self.sy, self.H, self.n)
 
 
 @dataclass

@@ -57,15 +57,17 @@ class SplitMix64:
 
 @dataclass(frozen=True)
 class Phase:
-    """J2 material with linear isotropic hardening (Section 4.2, n = 1)."""
+    """J2 material with isotropic hardening sigma_0 + H epbar^n (Section 4.2;
+    n = 1 is linear hardening)."""
 
     K: float        # bulk modulus
     G: float        # shear modulus
     sigma_y: float  # initial yield stress sigma_0
     H: float        # hardening modulus
+    n: float = 1.0  # hardening exponent (> 0)
 
     def as_tuple(self):
-        return (self.K, self.G, self.sigma_y, self.H)
+        return (self.K, self.G, self.sigma_y, self.H, self.n)
 
 
 # The two-phase material set used by every workload: bulk 0.833, shear 0.386,
