@@ -60,15 +60,18 @@ extern "C" {
 
 typedef struct fftg_handle fftg_handle;
 
-/* One material phase: J2 plasticity with linear isotropic hardening,
- * Section 4.2 with n = 1: C_e = K I(x)I + 2G I_d, yield function
- * Phi = sigma_eq - (sigma_y + H epbar). A phase with sigma_y >= 1e300 is
- * linear elastic. */
+/* One material phase: J2 plasticity with isotropic hardening, Section 4.2:
+ * C_e = K I(x)I + 2G I_d, yield function Phi = sigma_eq - (sigma_y + H epbar^n).
+ * n = 1 is linear hardening, whose return is in closed form; for other n the
+ * scalar return equation of Section 4.2 is solved for dgamma by a Newton
+ * iteration kept inside a bracket. A phase with sigma_y >= 1e300 is linear
+ * elastic. */
 typedef struct {
     double K;        /* bulk modulus, > 0 */
     double G;        /* shear modulus, > 0 */
     double sigma_y;  /* initial yield stress sigma_0, > 0 */
-    double H;        /* linear hardening modulus, >= 0 */
+    double H;        /* hardening modulus, >= 0 */
+    double n;        /* hardening exponent, > 0 (1: linear hardening) */
 } fftg_phase;
 
 typedef struct {
@@ -261,7 +264,10 @@ int fftg_server_stop(fftg_server* s);
  * It evaluates the J2 update of Section 4.2 at E + eps against the history
  * (eps_p, epbar), writes sigma [6][N^3] (and, where the pointers are not
  * NULL, the updated history and the compact tangent [7][N^3] in FP32
- * (FFTG_MIXED) or FP64 (FFTG_FP64)), and returns the homogenised stress
+ * (FFTG_MIXED) or FP64 (FFTG_FP64): per voxel K', 2G_eff, w11, w22, w23,
+ * w13, w12 with C = |K'| I(x)I + 2G_eff I_d - sign(K') w(x)w, where w33 =
+ * -(w11 + w22); K' < 0 marks a positive N(x)N coefficient, possible for
+ * hardening exponents n > 1), and returns the homogenised stress
  * mean(sigma) in sigma_mean[6] (host). Every field is a caller device buffer
  * in the unpadded layout [6][N^3] ([N^3] for epbar and phase).
  *

@@ -262,7 +262,7 @@ Layout make_layout(int N, int mixed, int nrhs, int B) {
         return at;
     };
     L.off_phase = take(Bs * cs);
-    L.off_mats = take(256 * 4 * 8);
+    L.off_mats = take(256 * fftg::kMatStride * 8);
     L.off_eps_star = take(Bs * 6 * cs * 8);
     L.off_eps_work = take(Bs * 6 * cs * 8);
     L.off_eps_p = take(Bs * 6 * cs * 8);
@@ -879,7 +879,7 @@ void fftg_default_options(fftg_options* o) {
     o->cg_graph = 1;
 }
 
-const char* fftg_version(void) { return "fftg 0.2 (sm_103a)"; }
+const char* fftg_version(void) { return "fftg 0.3 (sm_103a)"; }
 
 int fftg_workspace_size_batch(int N, int ncells, const fftg_options* opt, size_t* bytes) {
     if (!bytes || !valid_grid(N) || ncells < 1) return FFTG_EINVAL;
@@ -905,7 +905,8 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
         (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) || o.fixed_cg < 0 || o.fixed_newton < 0)
         return FFTG_EINVAL;
     for (int i = 0; i < nphase; ++i)
-        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0))
+        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0) ||
+            !(mats[i].n > 0) || !std::isfinite(mats[i].n))
             return FFTG_EINVAL;
     const size_t V = (size_t)N * N * N;
     for (size_t v = 0; v < V * (size_t)ncells; ++v)
@@ -984,12 +985,14 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     std::vector<double> tw64(2 * N);
     std::vector<float> tw32(2 * N);
     twiddles(N, tw64.data(), tw32.data());
-    std::vector<double> m(4 * nphase);
+    std::vector<double> m(fftg::kMatStride * nphase);
     for (int i = 0; i < nphase; ++i) {
-        m[4 * i] = mats[i].K;
-        m[4 * i + 1] = mats[i].G;
-        m[4 * i + 2] = mats[i].sigma_y;
-        m[4 * i + 3] = mats[i].H;
+        double* r = &m[fftg::kMatStride * i];
+        r[0] = mats[i].K;
+        r[1] = mats[i].G;
+        r[2] = mats[i].sigma_y;
+        r[3] = mats[i].H;
+        r[4] = mats[i].n;
     }
     cudaStream_t s = h->stream;
     bool ok = true;

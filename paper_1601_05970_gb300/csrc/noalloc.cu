@@ -31,10 +31,10 @@ constexpr int kMaxPhases = 256;
 constexpr int kPartialBlocks = fftg::kMaxPointwiseBlocks;  // grid cap of the kernel
 
 // Layout of the array: [partials: kPartialBlocks x 7 doubles]
-// [material table: kMaxPhases x 4 doubles] [NewtonDev: sums and ticket].
+// [material table: kMaxPhases x kMatStride doubles] [NewtonDev: sums and ticket].
 constexpr size_t kOffPartials = 0;
 constexpr size_t kOffMats = kOffPartials + (size_t)kPartialBlocks * 7 * sizeof(double);
-constexpr size_t kOffNd = kOffMats + (size_t)kMaxPhases * 4 * sizeof(double);
+constexpr size_t kOffNd = kOffMats + (size_t)kMaxPhases * fftg::kMatStride * sizeof(double);
 constexpr size_t kScratchBytes = ((kOffNd + sizeof(NewtonDev) + 255) / 256) * 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -73,7 +73,8 @@ extern "C" int fftg_constitutive_noalloc(int N, const double E[6], const double*
     if (!E || !eps_dev || !eps_p_dev || !epbar_dev || !phase_dev || !mats || !sigma_mean) return FFTG_EINVAL;
     if (tangent_dev && tangent_precision != FFTG_FP64 && tangent_precision != FFTG_MIXED) return FFTG_EINVAL;
     for (int i = 0; i < nphase; ++i)
-        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0))
+        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0) ||
+            !(mats[i].n > 0) || !(mats[i].n < 1e300))
             return FFTG_EINVAL;
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return FFTG_ECUDA;
@@ -82,16 +83,18 @@ extern "C" int fftg_constitutive_noalloc(int N, const double E[6], const double*
     double* partials = (double*)(b + kOffPartials);
     double* dmats = (double*)(b + kOffMats);
     NewtonDev* nd = (NewtonDev*)(b + kOffNd);
-    double m[kMaxPhases * 4];
+    double m[kMaxPhases * fftg::kMatStride];
     for (int i = 0; i < nphase; ++i) {
-        m[4 * i] = mats[i].K;
-        m[4 * i + 1] = mats[i].G;
-        m[4 * i + 2] = mats[i].sigma_y;
-        m[4 * i + 3] = mats[i].H;
+        double* r = m + fftg::kMatStride * i;
+        r[0] = mats[i].K;
+        r[1] = mats[i].G;
+        r[2] = mats[i].sigma_y;
+        r[3] = mats[i].H;
+        r[4] = mats[i].n;
     }
     // the ticket must start at zero; the rest of the array is overwritten
     if (cudaMemsetAsync(nd, 0, sizeof(NewtonDev), s) != cudaSuccess) return FFTG_ECUDA;
-    if (cudaMemcpyAsync(dmats, m, (size_t)nphase * 4 * sizeof(double), cudaMemcpyHostToDevice, s) !=
+    if (cudaMemcpyAsync(dmats, m, (size_t)nphase * fftg::kMatStride * sizeof(double), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return FFTG_ECUDA;
     ConstArgs a{};

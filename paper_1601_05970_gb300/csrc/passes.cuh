@@ -30,7 +30,7 @@ struct PassArgs {
     const void* aux;       // P1_CG: r; P5_DOT: p
     void* aux2;            // P1_CG: p (updated in place)
     void* aux3;            // P1_CG: x (gets the previous iteration's alpha p)
-    const void* tangent;   // [7][V]: K, 2G_eff, w11, w22, w23, w13, w12
+    const void* tangent;   // [7][V]: K', 2G_eff, w11, w22, w23, w13, w12 (see apply_tangent7)
     CGState* cg;           // per field, or null
     double* partials;      // [nf][nblocks][2]
     const void* tw;        // w_N^j, j < N, in the FFT precision
@@ -167,14 +167,20 @@ __device__ __forceinline__ void load_tw(cplx<T>* tw, const void* src, int n) {
 }
 
 // s = C : p with the compact J2 tangent (Section 4.2):
-// C = K I(x)I + 2G_eff I_d - w (x) w,  w = sqrt(-b) N, b < 0
+// C = |K'| I(x)I + 2G_eff I_d + b N(x)N, stored as w = sqrt(|b|) N and the
+// sign of b in the sign of K' (K > 0): K' > 0 for b <= 0, always the case
+// for hardening exponents n <= 1; K' < 0 for b > 0. w33 = -(w11 + w22).
 template <typename T>
 __device__ __forceinline__ void apply_tangent7(T K, T g2, T w0, T w1, T w3, T w4, T w5,
                                                const T (&p)[6], T (&s)[6]) {
     const T w2 = -(w0 + w1);
     const T tr = p[0] + p[1] + p[2];
     const T m = tr * T(1.0 / 3.0);
-    const T wp = w0 * p[0] + w1 * p[1] + w2 * p[2] + T(2) * (w3 * p[3] + w4 * p[4] + w5 * p[5]);
+    T wp = w0 * p[0] + w1 * p[1] + w2 * p[2] + T(2) * (w3 * p[3] + w4 * p[4] + w5 * p[5]);
+    if (K < T(0)) {
+        K = -K;
+        wp = -wp;
+    }
     const T kt = K * tr;
     s[0] = kt + g2 * (p[0] - m) - wp * w0;
     s[1] = kt + g2 * (p[1] - m) - wp * w1;

@@ -4,10 +4,15 @@
 // the reductions of the macroscopic tangent.
 #pragma once
 
+#include <cfloat>
+
 #include "common.cuh"
 #include "passes.cuh"
 
 namespace fftg {
+
+// Doubles per phase in the device material table: K, G, sigma_y, H, n.
+constexpr int kMatStride = 5;
 
 // Maximum grid of the grid-stride pointwise kernels (fixed per V, so the
 // reduction order never depends on timing).
@@ -34,7 +39,7 @@ struct ConstArgs {
     const double* eps_p;     // [6][V] committed plastic strain
     const double* epbar;     // [V] committed accumulated plastic strain
     const uint8_t* phase;    // [V]
-    const double* mats;      // [nphase][4] = K, G, sigma_y, H
+    const double* mats;      // [nphase][kMatStride] = K, G, sigma_y, H, n
     double* sigma;           // [6][V] out (may be null)
     double* eps_p_new;       // [6][V] out (may be null)
     double* epbar_new;       // [V] out (may be null)
@@ -53,12 +58,42 @@ struct ConstArgs {
     long long cell_tangent;  // stride of the tangent between cells
 };
 
-// Elastic predictor / plastic corrector with linear hardening (n = 1):
-// trial sigma = C_e : (eps - eps_p^t); Phi = sigma_eq - (sigma_y + H epbar^t);
-// if Phi > tie*sigma_y: dgamma = Phi / (3G + H), N = 3/2 s / sigma_eq,
-// eps_p += dgamma N, epbar += dgamma, sigma -= 2G dgamma N, and the tangent
-// C = C_e - 6G^2 dgamma/sigma_eq I_d + 4G^2 (dgamma/sigma_eq - 1/(3G+H)) N(x)N
-// stored as K, 2G_eff, w = sqrt(-b) N (b the N(x)N coefficient, negative).
+// Root dgamma of the scalar return equation of Section 4.2,
+//   seq - 3 G dgamma - sigma_0 - H (epbar_t + dgamma)^n = 0,
+// for a trial state with Phi_tr = phi > 0. The left side is positive at 0
+// and non-positive at phi / (3G) (the hardening term only grows), so the
+// root is bracketed there; Newton steps that leave the current bracket are
+// replaced by bisection. Stops when the step or the bracket is at the last
+// few bits, after at most 100 iterations.
+__device__ __forceinline__ double power_law_return(double seq, double eb, double G, double sy,
+                                                   double Hh, double n, double phi) {
+    double lo = 0.0, hi = phi / (3.0 * G);
+    double x = 0.5 * hi;
+    for (int k = 0; k < 100; ++k) {
+        const double y = eb + x;
+        const double yn = pow(y, n);
+        const double f = seq - 3.0 * G * x - sy - Hh * yn;
+        if (f > 0.0) lo = x; else hi = x;
+        const double df = -3.0 * G - (y > 0.0 ? n * Hh * yn / y : (double)INFINITY);
+        double xn = x - f / df;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        const bool done = fabs(xn - x) <= 4.0 * DBL_EPSILON * x || hi - lo <= 4.0 * DBL_EPSILON * hi;
+        x = xn;
+        if (done) break;
+    }
+    return x;
+}
+
+// Elastic predictor / plastic corrector (Section 4.2) with hardening
+// sigma_0 + H epbar^n:
+// trial sigma = C_e : (eps - eps_p^t); Phi = sigma_eq - (sigma_y + H (epbar^t)^n);
+// if Phi > tie*sigma_y: dgamma from the scalar return equation (closed form
+// Phi / (3G + H) for n = 1), N = 3/2 s / sigma_eq, eps_p += dgamma N,
+// epbar += dgamma, sigma -= 2G dgamma N, and the tangent
+// C = C_e - 6G^2 dgamma/sigma_eq I_d + 4G^2 (dgamma/sigma_eq - 1/(3G + h')) N(x)N,
+// h' = n H (epbar^t + dgamma)^(n-1), stored as K', 2G_eff, w = sqrt(|b|) N
+// with b the N(x)N coefficient and K' = K for b <= 0 (always for n <= 1),
+// K' = -K for b > 0.
 // Two blocks per SM (at most 128 registers): unbounded, the kernel takes
 // about 155 registers and runs one block per SM, 5 % slower at 243^3.
 template <typename TT>
@@ -84,8 +119,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
     for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
          v += (long long)gridDim.x * kThreads) {
         const int ph = phase[v];
-        const double K = a.mats[4 * ph], G = a.mats[4 * ph + 1], sy = a.mats[4 * ph + 2],
-                     Hh = a.mats[4 * ph + 3];
+        const double* mp = a.mats + kMatStride * ph;
+        const double K = mp[0], G = mp[1], sy = mp[2], Hh = mp[3], nh = mp[4];
         double e[6], ep[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -106,17 +141,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
         const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
                           2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
         const double seq = sqrt(1.5 * ss);
-        const double phi = seq - (sy + Hh * eb);
+        const bool linear = nh == 1.0;
+        const double phi = seq - (sy + Hh * (linear ? eb : pow(eb, nh)));
         double sig[6];
         double g2 = g2e;
         double w[6] = {0, 0, 0, 0, 0, 0};
         double dg = 0.0;
+        bool kneg = false;  // N(x)N coefficient positive (n > 1 only)
         if (phi > a.tie * sy) {
-            // one division gives both 1/sigma_eq and 1/(3G + H)
-            const double h3 = 3.0 * G + Hh;
-            const double rr = 1.0 / (seq * h3);
-            const double inv_seq = rr * h3, inv_h3 = rr * seq;
-            dg = phi * inv_h3;
+            double inv_seq, inv_h3;
+            if (linear) {
+                // one division gives both 1/sigma_eq and 1/(3G + H)
+                const double h3 = 3.0 * G + Hh;
+                const double rr = 1.0 / (seq * h3);
+                inv_seq = rr * h3;
+                inv_h3 = rr * seq;
+                dg = phi * inv_h3;
+            } else {
+                dg = power_law_return(seq, eb, G, sy, Hh, nh, phi);
+                const double y = eb + dg;  // > 0: dg > 0 on a plastic step
+                inv_seq = 1.0 / seq;
+                inv_h3 = 1.0 / (3.0 * G + nh * Hh * pow(y, nh - 1.0));
+            }
             const double f = 1.5 * inv_seq;
             const double gdg = g2e * dg;
             double Nn[6];
@@ -130,7 +176,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
             const double dgs = dg * inv_seq;
             g2 = g2e - 6.0 * G * G * dgs;
             const double b = 4.0 * G * G * (dgs - inv_h3);
-            const double sb = sqrt(fmax(-b, 0.0));
+            const double sb = sqrt(fabs(b));
+            if (b > 0.0) kneg = true;
 #pragma unroll
             for (int c = 0; c < 6; ++c) w[c] = sb * Nn[c];
         } else {
@@ -151,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
         }
         if (epbar_new) epbar_new[v] = eb + dg;
         if (tg) {
-            tg[v] = (TT)K;
+            tg[v] = (TT)(kneg ? -K : K);
             tg[cs + v] = (TT)g2;
             tg[2 * cs + v] = (TT)w[0];
             tg[3 * cs + v] = (TT)w[1];

@@ -49,7 +49,18 @@ class FftgError(RuntimeError):
 
 
 class fftg_phase(C.Structure):
-    _fields_ = [("K", C.c_double), ("G", C.c_double), ("sigma_y", C.c_double), ("H", C.c_double)]
+    _fields_ = [("K", C.c_double), ("G", C.c_double), ("sigma_y", C.c_double), ("H", C.c_double),
+                ("n", C.c_double)]
+
+
+def phase_array(mats):
+    """fftg_phase[] from materials: objects with as_tuple() or tuples
+    (K, G, sigma_y, H[, n]); n defaults to 1 (linear hardening)."""
+    rows = []
+    for t in mats:
+        t = tuple(map(float, t.as_tuple() if hasattr(t, "as_tuple") else t))
+        rows.append(fftg_phase(*(t if len(t) == 5 else t + (1.0,))))
+    return (fftg_phase * len(rows))(*rows)
 
 
 class fftg_options(C.Structure):
@@ -170,7 +181,7 @@ class Cell:
     PyTorch.
 
     phase: uint8 [N, N, N] (x1 slowest), or [ncells, N, N, N] for a batch;
-    mats: sequence of (K, G, sigma_y, H).
+    mats: sequence of (K, G, sigma_y, H[, n]) or Phase objects.
     """
 
     def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
@@ -205,8 +216,7 @@ class Cell:
         opt.workspace_bytes = nbytes
         self.precision = precision
         ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8).reshape(-1))
-        m = (fftg_phase * len(mats))(*[fftg_phase(*map(float, (t.as_tuple() if hasattr(t, "as_tuple") else t)))
-                                      for t in mats])
+        m = phase_array(mats)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.fftg_create_batch(C.byref(h), self.N, self.ncells,
@@ -357,8 +367,7 @@ class Server:
         opt.cg_inner_floor = cg_inner_floor
         opt.nrhs_tangent = 0
         opt.cg_graph = cg_graph
-        m = (fftg_phase * len(mats))(*[fftg_phase(*map(float, (t.as_tuple() if hasattr(t, "as_tuple") else t)))
-                                      for t in mats])
+        m = phase_array(mats)
         h = C.c_void_p()
         check(lib.fftg_server_start(C.byref(h), self.N, int(slots), len(mats), m, C.byref(opt),
                                     tol_newton, tol_cg), "fftg_server_start")

@@ -67,7 +67,7 @@ def test_noalloc_constitutive_matches_handle_call_twice(lib):
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
-    mats = (fftg.fftg_phase * 1)(fftg.fftg_phase(1.0, 0.5, 0.01, 0.0))
+    mats = (fftg.fftg_phase * 1)(fftg.fftg_phase(1.0, 0.5, 0.01, 0.0, 1.0))
     E = np.zeros(6)
     mean = np.zeros(6)
     dummy = C.c_void_p(1)  # never dereferenced: the size check comes first
