@@ -207,16 +207,38 @@ class J2Result:
                              # at the returned state (H for n = 1)
 
 
+MODEL_J2, MODEL_NLELASTIC, MODEL_VISCO = 0, 1, 2
+
+
+@dataclass
+class MatFields:
+    """Per-voxel material parameters (Section 4): bulk and shear moduli,
+    sigma_0, H, exponent n, eps_0, t_0 and the model id."""
+    K: np.ndarray
+    G: np.ndarray
+    sy: np.ndarray
+    H: np.ndarray
+    n: np.ndarray
+    eps0: np.ndarray
+    t0: np.ndarray
+    model: np.ndarray
+
+
 def material_fields(phase, mats):
-    """Per-voxel (K, G, sigma_y, H, n) arrays from a phase map; a material
-    given as (K, G, sigma_y, H) has n = 1."""
+    """Per-voxel parameters from a phase map. A material is an object with
+    as_tuple() or a tuple (K, G, sigma_y, H[, n]) (J2, n = 1 by default) or
+    (K, G, sigma_0, H, n, eps_0, t_0, model)."""
     rows = []
     for m in mats:
-        t = tuple(m.as_tuple() if hasattr(m, "as_tuple") else m)
-        rows.append(t if len(t) == 5 else t + (1.0,))
+        t = tuple(float(v) for v in (m.as_tuple() if hasattr(m, "as_tuple") else m))
+        if len(t) == 4:
+            t = t + (1.0,)
+        if len(t) == 5:
+            t = t + (0.0, 0.0, float(MODEL_J2))
+        rows.append(t)
     tab = np.array(rows, dtype=np.float64)
     ph = np.asarray(phase).astype(np.int64)
-    return tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4]
+    return MatFields(*(tab[ph, j] for j in range(7)), tab[ph, 7].astype(np.int64))
 
 
 def power_law_dgamma(seq_tr, epbar_t, G, sy, H, n, max_iter=200):
@@ -319,12 +341,155 @@ def j2_tangent(res: J2Result, sl=slice(None)):
     return C
 
 
+# --------------------------------------------------------------------------
+# Non-linear elasticity (Section 4.1)
+# --------------------------------------------------------------------------
+@dataclass
+class NLEResult:
+    sigma: np.ndarray        # [3, 3, ...]
+    eps_p: np.ndarray        # history, unchanged (the model has none)
+    epbar: np.ndarray
+    K: np.ndarray
+    s0: np.ndarray
+    e0: np.ndarray
+    n: np.ndarray
+    eeq: np.ndarray          # [...] equivalent strain
+    Nd: np.ndarray           # [3, 3, ...] N = 2/3 eps_d / eps_eq (0 where eps_eq = 0)
+
+
+def nonlinear_elastic_update(eps, eps_p_t, epbar_t, K, s0, e0, n):
+    """sigma = K tr(eps) I + sigma_0 (eps_eq / eps_0)^n N with
+    N = 2/3 eps_d / eps_eq and eps_eq = sqrt(2/3 eps_d : eps_d)
+    (Eqs. model:nlin:stress, model:nlin:N); no history."""
+    Ib = I2.reshape(3, 3, *([1] * (eps.ndim - 2)))
+    tr = eps[0, 0] + eps[1, 1] + eps[2, 2]
+    ed = eps - tr / 3.0 * Ib
+    eeq = np.sqrt(2.0 / 3.0 * np.sum(ed * ed, axis=(0, 1)))
+    safe = np.where(eeq > 0.0, eeq, 1.0)
+    Nd = np.where(eeq > 0.0, 2.0 / 3.0 * ed / safe, 0.0)
+    sigma = K * tr * Ib + s0 * (eeq / e0) ** n * Nd
+    return NLEResult(sigma, eps_p_t.copy(), np.array(epbar_t, dtype=np.float64, copy=True),
+                     K, s0, e0, n, eeq, Nd)
+
+
+def nle_tangent(res: NLEResult, sl=slice(None)):
+    """C = K I(x)I + sigma_0/eps_eq (eps_eq/eps_0)^n ((n - 1) N(x)N + 2/3 I_d)
+    (Eq. model:nlin-tangent). At eps_eq = 0 the factor sigma_0/eps_eq
+    (eps_eq/eps_0)^n is taken as its limit sigma_0/eps_0 for n = 1 and as 0
+    otherwise."""
+    K = res.K.reshape(-1)[sl]
+    s0 = res.s0.reshape(-1)[sl]
+    e0 = res.e0.reshape(-1)[sl]
+    n = res.n.reshape(-1)[sl]
+    eeq = res.eeq.reshape(-1)[sl]
+    Nd = res.Nd.reshape(3, 3, -1)[:, :, sl]
+    safe = np.where(eeq > 0.0, eeq, 1.0)
+    c = np.where(eeq > 0.0, s0 / safe * (eeq / e0) ** n, np.where(n == 1.0, s0 / e0, 0.0))
+    C = np.einsum("ijlm,v->ijlmv", II, K)
+    C += np.einsum("ijlm,v->ijlmv", I4d, 2.0 / 3.0 * c)
+    C += np.einsum("ijv,lmv,v->ijlmv", Nd, Nd, c * (n - 1.0))
+    return C
+
+
+# --------------------------------------------------------------------------
+# Visco-plasticity (Section 4.3)
+# --------------------------------------------------------------------------
+def visco_dgamma(seq_tr, G, s0, gdt, n, max_iter=200):
+    """Root of the implicit backward-Euler equation of Section 4.3,
+        dgamma = gamma_0 dt ((seq_tr - 3 G dgamma) / sigma_0)^(1/n),
+    gamma_0 = eps_0 / t_0, for seq_tr > 0: g(x) = x - gamma_0 dt ((seq_tr -
+    3 G x) / sigma_0)^(1/n) is increasing, negative at 0 and positive at
+    seq_tr / (3G); Newton steps leaving the bracket become bisections."""
+    seq_tr, G, s0, gdt, n = np.broadcast_arrays(
+        *(np.asarray(v, dtype=np.float64) for v in (seq_tr, G, s0, gdt, n)))
+    lo = np.zeros_like(seq_tr)
+    hi = seq_tr / (3.0 * G)
+    x = 0.5 * hi
+    for _ in range(max_iter):
+        u = np.maximum(seq_tr - 3.0 * G * x, 0.0) / s0
+        g = x - gdt * u ** (1.0 / n)
+        lo = np.where(g < 0.0, x, lo)
+        hi = np.where(g < 0.0, hi, x)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            dg = 1.0 + gdt / n * np.where(u > 0.0, u ** (1.0 / n - 1.0), np.inf) * 3.0 * G / s0
+            xn = x - g / dg
+        bad = ~((xn > lo) & (xn < hi)) | ~np.isfinite(xn)
+        xn = np.where(bad, 0.5 * (lo + hi), xn)
+        done = np.abs(xn - x) <= 4.0 * np.finfo(float).eps * np.maximum(np.abs(x), 1e-300)
+        x = xn
+        if np.all(done | (hi - lo <= 4.0 * np.finfo(float).eps * hi)):
+            break
+    return x
+
+
+def visco_update(eps, eps_p_t, epbar_t, K, G, s0, e0, t0, n, dt, tie=1e-12):
+    """Backward-Euler update of Section 4.3: the elastic trial state of
+    Section 4.2, then dgamma from `visco_dgamma` wherever seq_tr > tie
+    sigma_0 (there is no elastic range), and the corrector of Eq.
+    (model:plas:corrector). The consistent tangent has the form of the J2 one
+    with the slope n sigma_0 / (gamma_0 dt) (dgamma / (gamma_0 dt))^(n-1) in
+    place of the hardening slope, so the result is returned as a J2Result
+    whose `slope` holds it (`H` is unused)."""
+    Ib = I2.reshape(3, 3, *([1] * (eps.ndim - 2)))
+    ee = eps - eps_p_t
+    tr = ee[0, 0] + ee[1, 1] + ee[2, 2]
+    s = 2.0 * G * (ee - tr / 3.0 * Ib)
+    seq = np.sqrt(1.5 * np.sum(s * s, axis=(0, 1)))
+    flow = seq > tie * s0
+    safe = np.where(seq > 0.0, seq, 1.0)
+    Ntr = 1.5 * s / safe
+    gdt = e0 / t0 * dt
+    dgamma = np.zeros_like(seq)
+    if np.any(flow):
+        b = np.broadcast_arrays(seq, G, s0, gdt, n)
+        dgamma[flow] = visco_dgamma(*(v[flow] for v in b))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = dgamma / gdt
+        slope = np.where(flow, n * s0 / gdt * np.where(q > 0.0, q ** (n - 1.0), 0.0), 0.0)
+    eps_p = eps_p_t + dgamma * Ntr
+    epbar = epbar_t + dgamma
+    ee2 = eps - eps_p
+    tr2 = ee2[0, 0] + ee2[1, 1] + ee2[2, 2]
+    sigma = K * tr2 * Ib + 2.0 * G * (ee2 - tr2 / 3.0 * Ib)
+    return J2Result(sigma, eps_p, epbar, flow, dgamma, seq, Ntr, K, G,
+                    np.zeros_like(seq), slope)
+
+
+@dataclass
+class PointResult:
+    """Material update of a cell with several models: the fields, and per
+    model the voxels (flat indices) and that model's result on them."""
+    sigma: np.ndarray
+    eps_p: np.ndarray
+    epbar: np.ndarray
+    parts: list
+
+
+def point_tangent(res, sl=slice(None)):
+    """Consistent tangent [3, 3, 3, 3, M] of the voxels in `sl` (a slice of
+    the flat voxel index) for any of the results above."""
+    if isinstance(res, J2Result):
+        return j2_tangent(res, sl)
+    if isinstance(res, NLEResult):
+        return nle_tangent(res, sl)
+    V = res.epbar.size
+    idx = np.arange(V)[sl]
+    C = np.zeros((3, 3, 3, 3, idx.size))
+    pos = np.full(V, -1)
+    pos[idx] = np.arange(idx.size)
+    for vox, r in res.parts:
+        here = pos[vox] >= 0
+        if np.any(here):
+            C[..., pos[vox[here]]] = point_tangent(r, np.flatnonzero(here))
+    return C
+
+
 class Tangent:
     """The block-diagonal tangent D of Eq. (local_tangent), applied chunk-wise."""
 
     CHUNK = 1 << 16
 
-    def __init__(self, res: J2Result):
+    def __init__(self, res):
         self.res = res
         self.shape = res.sigma.shape[2:]
         self.V = int(np.prod(self.shape))
@@ -335,7 +500,7 @@ class Tangent:
         out = np.empty_like(pf)
         for s in range(0, self.V, self.CHUNK):
             sl = slice(s, min(s + self.CHUNK, self.V))
-            C = j2_tangent(self.res, sl)
+            C = point_tangent(self.res, sl)
             out[:, :, sl] = np.einsum("ijlmv,lmv->ijv", C, pf[:, :, sl])
         return out.reshape(p.shape)
 
@@ -394,10 +559,14 @@ class State:
     eps_star: np.ndarray = field(default=None)   # [3, 3, N, N, N]
     eps_p: np.ndarray = field(default=None)      # committed history
     epbar: np.ndarray = field(default=None)
+    dt: float = 1.0                              # time step of an increment
+                                                 # (rate-dependent models)
 
     def __post_init__(self):
         N = self.N
-        self.K, self.G, self.sy, self.H, self.n = material_fields(self.phase, self.mats)
+        self.mat = material_fields(self.phase, self.mats)
+        self.K, self.G, self.sy, self.H, self.n = (self.mat.K, self.mat.G, self.mat.sy,
+                                                   self.mat.H, self.mat.n)
         if self.E is None:
             self.E = np.zeros((3, 3))
         if self.eps_star is None:
@@ -408,8 +577,33 @@ class State:
             self.epbar = np.zeros((N, N, N))
 
     def constitutive(self, E, eps_star):
+        """The material update of Section 4 at E + eps*, voxel by voxel with
+        each voxel's model, against the committed history."""
         eps = eps_star + E[:, :, None, None, None]
-        return j2_update(eps, self.eps_p, self.epbar, self.K, self.G, self.sy, self.H, self.n)
+        mt = self.mat
+        if np.all(mt.model == MODEL_J2):
+            return j2_update(eps, self.eps_p, self.epbar, self.K, self.G, self.sy, self.H, self.n)
+        sigma = np.zeros_like(eps)
+        eps_p = self.eps_p.copy()
+        epbar = self.epbar.copy()
+        parts = []
+        for model in (MODEL_J2, MODEL_NLELASTIC, MODEL_VISCO):
+            m = mt.model == model
+            if not np.any(m):
+                continue
+            e, ep, eb = eps[:, :, m], self.eps_p[:, :, m], self.epbar[m]
+            if model == MODEL_J2:
+                r = j2_update(e, ep, eb, mt.K[m], mt.G[m], mt.sy[m], mt.H[m], mt.n[m])
+            elif model == MODEL_NLELASTIC:
+                r = nonlinear_elastic_update(e, ep, eb, mt.K[m], mt.sy[m], mt.eps0[m], mt.n[m])
+            else:
+                r = visco_update(e, ep, eb, mt.K[m], mt.G[m], mt.sy[m], mt.eps0[m], mt.t0[m],
+                                 mt.n[m], self.dt)
+            sigma[:, :, m] = r.sigma
+            eps_p[:, :, m] = r.eps_p
+            epbar[m] = r.epbar
+            parts.append((np.flatnonzero(m.reshape(-1)), r))
+        return PointResult(sigma, eps_p, epbar, parts)
 
 
 @dataclass

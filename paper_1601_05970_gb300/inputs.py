@@ -55,6 +55,10 @@ class SplitMix64:
         return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
 
 
+# Constitutive models of Section 4 (the `model` entry of a material tuple)
+MODEL_J2, MODEL_NLELASTIC, MODEL_VISCO = 0, 1, 2
+
+
 @dataclass(frozen=True)
 class Phase:
     """J2 material with isotropic hardening sigma_0 + H epbar^n (Section 4.2;
@@ -67,7 +71,53 @@ class Phase:
     n: float = 1.0  # hardening exponent (> 0)
 
     def as_tuple(self):
-        return (self.K, self.G, self.sigma_y, self.H, self.n)
+        """(K, G, sigma_0, H, n, eps_0, t_0, model), the field order of the
+        library's phase record."""
+        return (self.K, self.G, self.sigma_y, self.H, self.n, 0.0, 0.0, MODEL_J2)
+
+
+@dataclass(frozen=True)
+class NonlinearElastic:
+    """Non-linear elastic material of Section 4.1:
+    sigma = K tr(eps) I + sigma_0 (eps_eq / eps_0)^n N."""
+
+    K: float        # bulk modulus
+    sigma0: float   # reference stress sigma_0
+    eps0: float     # reference strain eps_0
+    n: float        # exponent
+
+    def as_tuple(self):
+        return (self.K, 0.0, self.sigma0, 0.0, self.n, self.eps0, 0.0, MODEL_NLELASTIC)
+
+
+@dataclass(frozen=True)
+class ViscoPlastic:
+    """Visco-plastic material of Section 4.3 (Norton's rule
+    gamma_dot = (eps_0 / t_0) (sigma_eq / sigma_0)^(1/n)) with the elasticity
+    of Section 4.2."""
+
+    K: float        # bulk modulus
+    G: float        # shear modulus
+    sigma0: float   # reference stress sigma_0
+    eps0: float     # reference strain eps_0
+    t0: float       # reference time t_0
+    n: float        # strain-rate sensitivity exponent
+
+    def as_tuple(self):
+        return (self.K, self.G, self.sigma0, 0.0, self.n, self.eps0, self.t0, MODEL_VISCO)
+
+
+def material_tuple(m):
+    """The 8-entry tuple (K, G, sigma_0, H, n, eps_0, t_0, model) of a material
+    given as an object with as_tuple() or as (K, G, sigma_y, H[, n]) (J2)."""
+    t = tuple(float(v) for v in (m.as_tuple() if hasattr(m, "as_tuple") else m))
+    if len(t) == 4:
+        t = t + (1.0,)
+    if len(t) == 5:
+        t = t + (0.0, 0.0, float(MODEL_J2))
+    if len(t) != 8:
+        raise ValueError(f"material {m!r}: expected 4, 5 or 8 entries")
+    return t
 
 
 # The two-phase material set used by every workload: bulk 0.833, shear 0.386,
