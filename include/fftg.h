@@ -60,18 +60,36 @@ extern "C" {
 
 typedef struct fftg_handle fftg_handle;
 
-/* One material phase: J2 plasticity with isotropic hardening, Section 4.2:
- * C_e = K I(x)I + 2G I_d, yield function Phi = sigma_eq - (sigma_y + H epbar^n).
- * n = 1 is linear hardening, whose return is in closed form; for other n the
- * scalar return equation of Section 4.2 is solved for dgamma by a Newton
- * iteration kept inside a bracket. A phase with sigma_y >= 1e300 is linear
- * elastic. */
+/* Constitutive models of Section 4 (fftg_phase.model). */
+#define FFTG_MODEL_J2 0          /* J2 elasto-plasticity, Section 4.2 */
+#define FFTG_MODEL_NLELASTIC 1   /* non-linear elasticity, Section 4.1 */
+#define FFTG_MODEL_VISCO 2       /* visco-plasticity, Section 4.3 */
+
+/* One material phase.
+ * FFTG_MODEL_J2 (Section 4.2): C_e = K I(x)I + 2G I_d, yield function
+ *   Phi = sigma_eq - (sigma_y + H epbar^n). n = 1 is linear hardening, whose
+ *   return is in closed form; for other n the scalar return equation is
+ *   solved for dgamma by a Newton iteration kept inside a bracket. A phase
+ *   with sigma_y >= 1e300 is linear elastic. Uses K, G, sigma_y, H, n.
+ * FFTG_MODEL_NLELASTIC (Section 4.1): sigma = K tr(eps) I +
+ *   sigma_y (eps_eq / eps0)^n N, N = 2/3 eps_d / eps_eq; no history. Uses
+ *   K, sigma_y (the reference stress sigma_0), eps0, n.
+ * FFTG_MODEL_VISCO (Section 4.3): the elasticity of Section 4.2 with
+ *   Norton's rule gamma_dot = (eps0 / t0) (sigma_eq / sigma_y)^(1/n),
+ *   integrated by backward Euler over the time step fftg_options.dt of each
+ *   increment. Uses K, G, sigma_y (the reference stress), eps0, t0, n.
+ * Parameters a model does not use are ignored. */
 typedef struct {
     double K;        /* bulk modulus, > 0 */
-    double G;        /* shear modulus, > 0 */
-    double sigma_y;  /* initial yield stress sigma_0, > 0 */
-    double H;        /* hardening modulus, >= 0 */
-    double n;        /* hardening exponent, > 0 (1: linear hardening) */
+    double G;        /* shear modulus, > 0 (J2, VISCO) */
+    double sigma_y;  /* J2: initial yield stress sigma_0; NLELASTIC, VISCO:
+                        reference stress sigma_0; > 0 */
+    double H;        /* J2: hardening modulus, >= 0 */
+    double n;        /* J2: hardening exponent; NLELASTIC: exponent; VISCO:
+                        strain-rate sensitivity; > 0 */
+    double eps0;     /* NLELASTIC, VISCO: reference strain eps_0, > 0 */
+    double t0;       /* VISCO: reference time t_0, > 0 */
+    int    model;    /* FFTG_MODEL_* (0 = J2) */
 } fftg_phase;
 
 typedef struct {
@@ -98,6 +116,8 @@ typedef struct {
                                (no host round trip per iteration); 0: enqueue
                                iterations in chunks from the host. Profiling
                                (fftg_profile_enable) uses the chunked path. */
+    double dt;              /* time step of each increment, for rate-dependent
+                               phases (FFTG_MODEL_VISCO), > 0 (default 1) */
 } fftg_options;
 
 /* Per-increment diagnostics of the last fftg_step (Algorithm 1). */
@@ -261,18 +281,20 @@ int fftg_server_stop(fftg_server* s);
  * call cudaMalloc: the call fails while the pool holds the memory, or it
  * stalls the whole device. This call needs no handle and no workspace.
  *
- * It evaluates the J2 update of Section 4.2 at E + eps against the history
- * (eps_p, epbar), writes sigma [6][N^3] (and, where the pointers are not
+ * It evaluates the material update of Section 4 at E + eps against the
+ * history (eps_p, epbar); rate-dependent phases (FFTG_MODEL_VISCO, which
+ * need a time step) are not accepted here (FFTG_EINVAL). It writes
+ * sigma [6][N^3] (and, where the pointers are not
  * NULL, the updated history and the compact tangent [7][N^3] in FP32
  * (FFTG_MIXED) or FP64 (FFTG_FP64): per voxel K', 2G_eff, w11, w22, w23,
  * w13, w12 with C = |K'| I(x)I + 2G_eff I_d - sign(K') w(x)w, where w33 =
  * -(w11 + w22); K' < 0 marks a positive N(x)N coefficient, possible for
- * hardening exponents n > 1), and returns the homogenised stress
+ * exponents n > 1), and returns the homogenised stress
  * mean(sigma) in sigma_mean[6] (host). Every field is a caller device buffer
  * in the unpadded layout [6][N^3] ([N^3] for epbar and phase).
  *
  * Its scratch (block partial sums, the reduction ticket, the material table)
- * is one fixed array of about 240 KB compiled into the library, held by every
+ * is one fixed array of about 250 KB compiled into the library, held by every
  * GPU that loads it until the process exits. Limits: N <= 243, nphase <= 256;
  * larger values return FFTG_EINVAL. The first call on a device looks up the
  * array's device address (once per device, with that device current): make

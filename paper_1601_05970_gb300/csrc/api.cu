@@ -17,6 +17,7 @@
 
 #include "../../include/fftg.h"
 #include "driver.h"
+#include "materials.h"
 #include "passes.cuh"
 #include "pointwise.cuh"
 
@@ -367,6 +368,7 @@ static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, 
     a.nd = h->nd + cell0;
     a.cg = cg ? cg + cell0 : nullptr;
     a.tie = 1e-12;
+    a.dt = h->opt.dt;
     a.active = mask_dev ? mask_dev + cell0 : nullptr;
     a.cell_fields = 6 * h->cs;
     a.cell_scalar = h->cs;
@@ -877,9 +879,10 @@ void fftg_default_options(fftg_options* o) {
     o->cg_inner_floor = 1e-6;
     o->nrhs_tangent = 6;
     o->cg_graph = 1;
+    o->dt = 1.0;
 }
 
-const char* fftg_version(void) { return "fftg 0.3 (sm_103a)"; }
+const char* fftg_version(void) { return "fftg 0.4 (sm_103a)"; }
 
 int fftg_workspace_size_batch(int N, int ncells, const fftg_options* opt, size_t* bytes) {
     if (!bytes || !valid_grid(N) || ncells < 1) return FFTG_EINVAL;
@@ -902,12 +905,11 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     fftg_options o;
     if (opt) o = *opt; else fftg_default_options(&o);
     if ((o.precision != FFTG_FP64 && o.precision != FFTG_MIXED) || o.max_newton < 1 || o.max_cg < 1 ||
-        (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) || o.fixed_cg < 0 || o.fixed_newton < 0)
+        (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) || o.fixed_cg < 0 || o.fixed_newton < 0 ||
+        !fftg::pos_finite(o.dt))
         return FFTG_EINVAL;
     for (int i = 0; i < nphase; ++i)
-        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0) ||
-            !(mats[i].n > 0) || !std::isfinite(mats[i].n))
-            return FFTG_EINVAL;
+        if (!fftg::phase_valid(mats[i], true)) return FFTG_EINVAL;
     const size_t V = (size_t)N * N * N;
     for (size_t v = 0; v < V * (size_t)ncells; ++v)
         if (phase[v] >= nphase) return FFTG_EINVAL;
@@ -986,14 +988,7 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     std::vector<float> tw32(2 * N);
     twiddles(N, tw64.data(), tw32.data());
     std::vector<double> m(fftg::kMatStride * nphase);
-    for (int i = 0; i < nphase; ++i) {
-        double* r = &m[fftg::kMatStride * i];
-        r[0] = mats[i].K;
-        r[1] = mats[i].G;
-        r[2] = mats[i].sigma_y;
-        r[3] = mats[i].H;
-        r[4] = mats[i].n;
-    }
+    for (int i = 0; i < nphase; ++i) fftg::pack_phase(mats[i], &m[fftg::kMatStride * i]);
     cudaStream_t s = h->stream;
     bool ok = true;
     for (int b = 0; b < ncells && ok; ++b)

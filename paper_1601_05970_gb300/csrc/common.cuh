@@ -8,6 +8,11 @@ namespace fftg {
 
 constexpr int kThreads = 256;
 
+// Device material table: per phase K, G, sigma_0, H, n, eps_0, t_0, model
+// (the fields of fftg_phase, the model id as a double).
+constexpr int kMatStride = 8;
+enum : int { MODEL_J2 = 0, MODEL_NLELASTIC = 1, MODEL_VISCO = 2 };
+
 // Roundoff floor (relative to the norm of the projected field) below which a
 // CG residual is treated as FFT roundoff; see the CG readings.
 constexpr double kRoundoffRel = 1e-13;

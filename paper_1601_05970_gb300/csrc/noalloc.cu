@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "../../include/fftg.h"
+#include "materials.h"
 #include "pointwise.cuh"
 
 namespace {
@@ -73,9 +74,7 @@ extern "C" int fftg_constitutive_noalloc(int N, const double E[6], const double*
     if (!E || !eps_dev || !eps_p_dev || !epbar_dev || !phase_dev || !mats || !sigma_mean) return FFTG_EINVAL;
     if (tangent_dev && tangent_precision != FFTG_FP64 && tangent_precision != FFTG_MIXED) return FFTG_EINVAL;
     for (int i = 0; i < nphase; ++i)
-        if (!(mats[i].K > 0) || !(mats[i].G > 0) || !(mats[i].sigma_y > 0) || !(mats[i].H >= 0) ||
-            !(mats[i].n > 0) || !(mats[i].n < 1e300))
-            return FFTG_EINVAL;
+        if (!fftg::phase_valid(mats[i], false)) return FFTG_EINVAL;
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return FFTG_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -84,14 +83,7 @@ extern "C" int fftg_constitutive_noalloc(int N, const double E[6], const double*
     double* dmats = (double*)(b + kOffMats);
     NewtonDev* nd = (NewtonDev*)(b + kOffNd);
     double m[kMaxPhases * fftg::kMatStride];
-    for (int i = 0; i < nphase; ++i) {
-        double* r = m + fftg::kMatStride * i;
-        r[0] = mats[i].K;
-        r[1] = mats[i].G;
-        r[2] = mats[i].sigma_y;
-        r[3] = mats[i].H;
-        r[4] = mats[i].n;
-    }
+    for (int i = 0; i < nphase; ++i) fftg::pack_phase(mats[i], m + fftg::kMatStride * i);
     // the ticket must start at zero; the rest of the array is overwritten
     if (cudaMemsetAsync(nd, 0, sizeof(NewtonDev), s) != cudaSuccess) return FFTG_ECUDA;
     if (cudaMemcpyAsync(dmats, m, (size_t)nphase * fftg::kMatStride * sizeof(double), cudaMemcpyHostToDevice, s) !=
@@ -114,6 +106,7 @@ extern "C" int fftg_constitutive_noalloc(int N, const double E[6], const double*
     a.nd = nd;
     a.cg = nullptr;
     a.tie = 1e-12;
+    a.dt = 1.0;  // unused: no rate-dependent phases here
     const int nb = fftg::pointwise_blocks(a.V);
     if (tangent_dev && tangent_precision == FFTG_FP64)
         fftg::k_constitutive<double><<<nb, fftg::kThreads, 0, s>>>(a);

@@ -11,9 +11,6 @@
 
 namespace fftg {
 
-// Doubles per phase in the device material table: K, G, sigma_y, H, n.
-constexpr int kMatStride = 5;
-
 // Maximum grid of the grid-stride pointwise kernels (fixed per V, so the
 // reduction order never depends on timing).
 constexpr int kMaxPointwiseBlocks = 4096;
@@ -39,7 +36,7 @@ struct ConstArgs {
     const double* eps_p;     // [6][V] committed plastic strain
     const double* epbar;     // [V] committed accumulated plastic strain
     const uint8_t* phase;    // [V]
-    const double* mats;      // [nphase][kMatStride] = K, G, sigma_y, H, n
+    const double* mats;      // [nphase][kMatStride]: K, G, sigma_0, H, n, eps_0, t_0, model
     double* sigma;           // [6][V] out (may be null)
     double* eps_p_new;       // [6][V] out (may be null)
     double* epbar_new;       // [V] out (may be null)
@@ -48,6 +45,7 @@ struct ConstArgs {
     NewtonDev* nd;           // sig2 and sum of sigma
     CGState* cg;             // if set: cg->floor2 from ||sigma||
     double tie;              // plastic iff Phi_trial > tie * sigma_y
+    double dt;               // time step of the increment (visco-plastic phases)
     // Batches of cells: cell = blockIdx.y; per-cell offsets below (0 for a
     // single cell). Edev [cells][6] replaces E when set; active[cell] == 0
     // skips the cell.
@@ -84,8 +82,10 @@ __device__ __forceinline__ double power_law_return(double seq, double eb, double
     return x;
 }
 
-// Elastic predictor / plastic corrector (Section 4.2) with hardening
-// sigma_0 + H epbar^n:
+// Material update at every voxel by its phase's model: non-linear
+// elasticity (Section 4.1), or for J2 (Section 4.2, hardening
+// sigma_0 + H epbar^n) and visco-plasticity (Section 4.3) the elastic
+// predictor / plastic corrector:
 // trial sigma = C_e : (eps - eps_p^t); Phi = sigma_eq - (sigma_y + H (epbar^t)^n);
 // if Phi > tie*sigma_y: dgamma from the scalar return equation (closed form
 // Phi / (3G + H) for n = 1), N = 3/2 s / sigma_eq, eps_p += dgamma N,
@@ -120,69 +120,102 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
          v += (long long)gridDim.x * kThreads) {
         const int ph = phase[v];
         const double* mp = a.mats + kMatStride * ph;
-        const double K = mp[0], G = mp[1], sy = mp[2], Hh = mp[3], nh = mp[4];
+        const double K = mp[0], G = mp[1], sy = mp[2], nh = mp[4];
+        const int model = (int)mp[7];
+        // elastic trial strain; the non-linear elastic model uses the total
+        // strain (it has no plastic strain; eps_p passes through unchanged)
+        const bool nle = model == MODEL_NLELASTIC;
         double e[6], ep[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             ep[c] = eps_p[c * cs + v];
-            e[c] = E[c] + eps[c * cs + v] - ep[c];
+            e[c] = E[c] + eps[c * cs + v] - (nle ? 0.0 : ep[c]);
         }
         const double eb = epbar[v];
         const double tr = e[0] + e[1] + e[2];
         const double m = tr * (1.0 / 3.0);
-        const double g2e = 2.0 * G;
-        double s[6];
-        s[0] = g2e * (e[0] - m);
-        s[1] = g2e * (e[1] - m);
-        s[2] = g2e * (e[2] - m);
-        s[3] = g2e * e[3];
-        s[4] = g2e * e[4];
-        s[5] = g2e * e[5];
-        const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
-                          2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
-        const double seq = sqrt(1.5 * ss);
-        const bool linear = nh == 1.0;
-        const double phi = seq - (sy + Hh * (linear ? eb : pow(eb, nh)));
         double sig[6];
-        double g2 = g2e;
+        double g2;
         double w[6] = {0, 0, 0, 0, 0, 0};
         double dg = 0.0;
-        bool kneg = false;  // N(x)N coefficient positive (n > 1 only)
-        if (phi > a.tie * sy) {
-            double inv_seq, inv_h3;
-            if (linear) {
-                // one division gives both 1/sigma_eq and 1/(3G + H)
-                const double h3 = 3.0 * G + Hh;
-                const double rr = 1.0 / (seq * h3);
-                inv_seq = rr * h3;
-                inv_h3 = rr * seq;
-                dg = phi * inv_h3;
-            } else {
-                dg = power_law_return(seq, eb, G, sy, Hh, nh, phi);
-                const double y = eb + dg;  // > 0: dg > 0 on a plastic step
-                inv_seq = 1.0 / seq;
-                inv_h3 = 1.0 / (3.0 * G + nh * Hh * pow(y, nh - 1.0));
-            }
-            const double f = 1.5 * inv_seq;
-            const double gdg = g2e * dg;
-            double Nn[6];
+        bool kneg = false;  // N(x)N coefficient of the tangent positive
+        if (nle) {
+            // Section 4.1: sigma_d = sigma_0 (eps_eq/eps_0)^n N, N = 2/3 d/eps_eq,
+            // d = dev(eps), eps_eq = sqrt(2/3 d:d); tangent
+            // c ((n - 1) N(x)N + 2/3 I_d), c = sigma_0/eps_eq (eps_eq/eps_0)^n,
+            // whose limit at eps_eq = 0 is taken as sigma_0/eps_0 for n = 1, else 0
+            const double d[6] = {e[0] - m, e[1] - m, e[2] - m, e[3], e[4], e[5]};
+            const double eeq = sqrt((2.0 / 3.0) * frob<double>(d, d));
+            const double e0r = mp[5];
+            const double c = eeq > 0.0 ? sy / eeq * pow(eeq / e0r, nh) : (nh == 1.0 ? sy / e0r : 0.0);
+            g2 = (2.0 / 3.0) * c;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
+            for (int k = 0; k < 6; ++k) sig[k] = g2 * d[k];
+            const double b = c * (nh - 1.0);
+            kneg = b > 0.0;
+            const double sbN = eeq > 0.0 ? sqrt(fabs(b)) * (2.0 / 3.0) / eeq : 0.0;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                sig[c] = s[c] - gdg * Nn[c];
-                ep[c] += dg * Nn[c];
-            }
-            const double dgs = dg * inv_seq;
-            g2 = g2e - 6.0 * G * G * dgs;
-            const double b = 4.0 * G * G * (dgs - inv_h3);
-            const double sb = sqrt(fabs(b));
-            if (b > 0.0) kneg = true;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) w[c] = sb * Nn[c];
+            for (int k = 0; k < 6; ++k) w[k] = sbN * d[k];
         } else {
+            // J2 (Section 4.2) or visco-plasticity (Section 4.3), elastic
+            // trial state. The visco-plastic backward-Euler equation
+            // seq - 3G dgamma = sigma_0 (dgamma / (gamma_0 dt))^n has the
+            // form of the J2 return with no yield stress, no history in the
+            // rate term and H = sigma_0 (gamma_0 dt)^(-n), gamma_0 = eps_0/t_0.
+            const bool visco = model == MODEL_VISCO;
+            const double g2e = 2.0 * G;
+            double s[6];
+            s[0] = g2e * (e[0] - m);
+            s[1] = g2e * (e[1] - m);
+            s[2] = g2e * (e[2] - m);
+            s[3] = g2e * e[3];
+            s[4] = g2e * e[4];
+            s[5] = g2e * e[5];
+            const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
+                              2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+            const double seq = sqrt(1.5 * ss);
+            const double sy_h = visco ? 0.0 : sy;
+            const double Hh = visco ? sy * pow(mp[5] / mp[6] * a.dt, -nh) : mp[3];
+            const double eb_h = visco ? 0.0 : eb;
+            const bool linear = nh == 1.0;
+            const double phi = seq - (sy_h + Hh * (linear ? eb_h : pow(eb_h, nh)));
+            g2 = g2e;
+            if (phi > a.tie * sy) {
+                double inv_seq, inv_h3;
+                if (linear) {
+                    // one division gives both 1/sigma_eq and 1/(3G + H)
+                    const double h3 = 3.0 * G + Hh;
+                    const double rr = 1.0 / (seq * h3);
+                    inv_seq = rr * h3;
+                    inv_h3 = rr * seq;
+                    dg = phi * inv_h3;
+                } else {
+                    dg = power_law_return(seq, eb_h, G, sy_h, Hh, nh, phi);
+                    const double y = eb_h + dg;  // > 0: dg > 0 on a plastic step
+                    inv_seq = 1.0 / seq;
+                    inv_h3 = 1.0 / (3.0 * G + nh * Hh * pow(y, nh - 1.0));
+                }
+                const double f = 1.5 * inv_seq;
+                const double gdg = g2e * dg;
+                double Nn[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) sig[c] = s[c];
+                for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    sig[c] = s[c] - gdg * Nn[c];
+                    ep[c] += dg * Nn[c];
+                }
+                const double dgs = dg * inv_seq;
+                g2 = g2e - 6.0 * G * G * dgs;
+                const double b = 4.0 * G * G * (dgs - inv_h3);
+                const double sb = sqrt(fabs(b));
+                if (b > 0.0) kneg = true;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) w[c] = sb * Nn[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sig[c] = s[c];
+            }
         }
         const double kt = K * tr;
         sig[0] += kt;

@@ -50,16 +50,18 @@ class FftgError(RuntimeError):
 
 class fftg_phase(C.Structure):
     _fields_ = [("K", C.c_double), ("G", C.c_double), ("sigma_y", C.c_double), ("H", C.c_double),
-                ("n", C.c_double)]
+                ("n", C.c_double), ("eps0", C.c_double), ("t0", C.c_double), ("model", C.c_int)]
 
 
 def phase_array(mats):
-    """fftg_phase[] from materials: objects with as_tuple() or tuples
-    (K, G, sigma_y, H[, n]); n defaults to 1 (linear hardening)."""
+    """fftg_phase[] from materials: objects with as_tuple() (inputs.Phase,
+    NonlinearElastic, ViscoPlastic) or tuples (K, G, sigma_y, H[, n]) of a
+    J2 phase, n = 1 by default."""
+    from . import inputs
     rows = []
-    for t in mats:
-        t = tuple(map(float, t.as_tuple() if hasattr(t, "as_tuple") else t))
-        rows.append(fftg_phase(*(t if len(t) == 5 else t + (1.0,))))
+    for m in mats:
+        t = inputs.material_tuple(m)
+        rows.append(fftg_phase(*t[:7], int(t[7])))
     return (fftg_phase * len(rows))(*rows)
 
 
@@ -67,7 +69,7 @@ class fftg_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_newton", C.c_int), ("max_cg", C.c_int),
                 ("cg_inner_floor", C.c_double), ("fixed_cg", C.c_int), ("fixed_newton", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("nrhs_tangent", C.c_int), ("cg_graph", C.c_int)]
+                ("nrhs_tangent", C.c_int), ("cg_graph", C.c_int), ("dt", C.c_double)]
 
 
 class fftg_result(C.Structure):
@@ -186,7 +188,7 @@ class Cell:
 
     def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
                  cg_inner_floor=1e-6, fixed_cg=0, fixed_newton=0, nrhs_tangent=6,
-                 device=None, stream=None, cg_graph=1):
+                 device=None, stream=None, cg_graph=1, dt=1.0):
         import torch
 
         lib = load()
@@ -203,6 +205,7 @@ class Cell:
         opt.fixed_newton = fixed_newton
         opt.nrhs_tangent = nrhs_tangent
         opt.cg_graph = cg_graph
+        opt.dt = dt
         self.device = torch.device(device or "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -357,10 +360,11 @@ class Server:
     """
 
     def __init__(self, N, slots, mats, precision="mixed", tol_newton=1e-5, tol_cg=1e-8,
-                 max_newton=50, max_cg=2000, cg_inner_floor=1e-6, cg_graph=1):
+                 max_newton=50, max_cg=2000, cg_inner_floor=1e-6, cg_graph=1, dt=1.0):
         lib = load()
         self.N = int(N)
         opt = default_options()
+        opt.dt = dt
         opt.precision = FFTG_MIXED if precision == "mixed" else FFTG_FP64
         opt.max_newton = max_newton
         opt.max_cg = max_cg
