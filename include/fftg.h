@@ -47,6 +47,9 @@ extern "C" {
 #define FFTG_ESTATE          -7  /* call out of order (e.g. tangent before any step) */
 
 /* ---------------------------------------------------------------- precision */
+#define FFTG_SOLVER_CG 0          /* conjugate gradients (Section 2.5) */
+#define FFTG_SOLVER_RICHARDSON 1  /* basic scheme (Section 3.4), comparison only */
+
 #define FFTG_FP64   0  /* every step in FP64 */
 #define FFTG_MIXED  1  /* FP32 inner CG (FFT, projection, tangent contraction);
                           FP64 return mapping, residual G sigma, Newton test and
@@ -118,6 +121,17 @@ typedef struct {
                                (fftg_profile_enable) uses the chunked path. */
     double dt;              /* time step of each increment, for rate-dependent
                                phases (FFTG_MODEL_VISCO), > 0 (default 1) */
+    int    solver;          /* linear solver of each Newton iteration (and of
+                               fftg_tangent): FFTG_SOLVER_CG (default), or
+                               FFTG_SOLVER_RICHARDSON, the basic scheme of
+                               Section 3.4 as a comparison: Richardson's
+                               iteration with the reference medium
+                               C_ref = (lambda_min + lambda_max)/2 I_s updated
+                               at every Newton iteration from the extreme
+                               eigenvalues of the local tangents. It needs
+                               positive definite tangents (else FFTG_ENAN) and
+                               takes O(lambda_max/lambda_min) iterations where
+                               CG takes O(sqrt(lambda_max/lambda_min)). */
 } fftg_options;
 
 /* Per-increment diagnostics of the last fftg_step (Algorithm 1). */

@@ -548,6 +548,67 @@ def cg(apply_A, b, tol, max_iter=2000, fixed_iters=None, floor=0.0):
 
 
 # --------------------------------------------------------------------------
+# The basic scheme (Section 3.4): Richardson's iteration with a reference
+# medium, as a comparison solver for the same linear system
+# --------------------------------------------------------------------------
+def mandel(C):
+    """6x6 matrices [6, 6, M] of tangents C [3, 3, 3, 3, M] in the Mandel
+    basis (shear components scaled by sqrt 2), whose eigenvalues are those
+    of C acting on symmetric tensors with the Frobenius product."""
+    w = np.array([1.0, 1.0, 1.0, np.sqrt(2.0), np.sqrt(2.0), np.sqrt(2.0)])
+    M = np.empty((6, 6, C.shape[-1]))
+    for a, (i, j) in enumerate(PAIRS):
+        for b, (l, m) in enumerate(PAIRS):
+            M[a, b] = w[a] * w[b] * C[i, j, l, m]
+    return M
+
+
+def tangent_bounds(res):
+    """lambda_min and lambda_max of the local tangents over the grid
+    (Section 3.4), from the eigenvalues of each voxel's 6x6 matrix."""
+    V = res.epbar.size
+    lo, hi = np.inf, -np.inf
+    for s0 in range(0, V, Tangent.CHUNK):
+        M = mandel(point_tangent(res, slice(s0, min(s0 + Tangent.CHUNK, V))))
+        ev = np.linalg.eigvalsh(np.moveaxis(M, -1, 0))
+        lo, hi = min(lo, ev.min()), max(hi, ev.max())
+    return float(lo), float(hi)
+
+
+def richardson(apply_A, b, omega, tol, max_iter=2000, floor=0.0):
+    """Richardson's iteration x_{k+1} = x_k + omega (b - A x_k), x_0 = 0.
+
+    With the reference medium C_ref = c I_s, c = (lambda_min + lambda_max)/2,
+    Gamma_ref = G / c (Appendix A) and the basic scheme's update
+    x + Gamma_ref (-sigma - D x) is this iteration on G D x = -G sigma with
+    omega = 1 / c. Stops when ||b - A x_k|| <= max(tol ||b||, floor).
+    Returns (x, iterations, final relative residual).
+    """
+    x = np.zeros_like(b)
+    r = b.copy()
+    rr0 = inner(r, r)
+    if rr0 == 0.0:
+        return x, 0, 0.0
+    stop2 = max(tol * tol * rr0, floor * floor)
+    rr = rr0
+    it = 0
+    while rr > stop2 and it < max_iter:
+        x += omega * r
+        r = b - apply_A(x)
+        rr = inner(r, r)
+        it += 1
+    return x, it, float(np.sqrt(rr / rr0))
+
+
+def linear_solve(solver, tan, res, rhs, tol, max_iter, floor, fixed_iters=None):
+    """G C x = rhs by CG (solver 'cg') or by the basic scheme ('richardson')."""
+    if solver == "cg":
+        return cg(lambda p: matvec(tan, p), rhs, tol, max_iter, fixed_iters=fixed_iters, floor=floor)
+    lo, hi = tangent_bounds(res)
+    return richardson(lambda p: matvec(tan, p), rhs, 2.0 / (lo + hi), tol, max_iter, floor=floor)
+
+
+# --------------------------------------------------------------------------
 # Algorithm 1: incremental-iterative Newton-CG
 # --------------------------------------------------------------------------
 @dataclass
@@ -618,7 +679,7 @@ class StepResult:
 
 
 def solve_increment(st: State, dE6, tol_newton, tol_cg, max_newton=50,
-                    max_cg=2000, fixed_cg=None, fixed_newton=None):
+                    max_cg=2000, fixed_cg=None, fixed_newton=None, solver="cg"):
     """One increment of Algorithm 1 (increment loop body).
 
     E_t+dt = E_t + dE; Newton on G sigma(E + eps*) = 0 starting from the
@@ -645,8 +706,8 @@ def solve_increment(st: State, dE6, tol_newton, tol_cg, max_newton=50,
         if nG <= ROUNDOFF_RHS * ns:
             de, ncg = np.zeros_like(Gs), 0
         else:
-            de, ncg, _ = cg(lambda p: matvec(tan, p), -Gs, tol_cg, max_cg,
-                            fixed_iters=fixed_cg, floor=ROUNDOFF_RHS * ns)
+            de, ncg, _ = linear_solve(solver, tan, res, -Gs, tol_cg, max_cg,
+                                      ROUNDOFF_RHS * ns, fixed_iters=fixed_cg)
         eps_star += de
         it += 1
         cg_total += ncg
@@ -674,7 +735,7 @@ def solve_increment(st: State, dE6, tol_newton, tol_cg, max_newton=50,
     return StepResult(Sigma, it, cg_total, cg_list, res_list, nn_list, converged)
 
 
-def macro_tangent(st: State, tol_cg, max_cg=2000):
+def macro_tangent(st: State, tol_cg, max_cg=2000, solver="cg"):
     """6x6 algorithmic macroscopic tangent dSigma/dE at the committed state.
 
     Not in the paper. Column j perturbs tensor component j (a shear perturbs
@@ -695,8 +756,8 @@ def macro_tangent(st: State, tol_cg, max_cg=2000):
         Ef = np.broadcast_to(Ej[:, :, None, None, None], (3, 3, N, N, N)).copy()
         CE = tan.apply(Ef)
         rhs = -project(CE)
-        de, _, _ = cg(lambda p: matvec(tan, p), rhs, tol_cg, max_cg,
-                      floor=ROUNDOFF_RHS * np.sqrt(inner(CE, CE)))
+        de, _, _ = linear_solve(solver, tan, res, rhs, tol_cg, max_cg,
+                                ROUNDOFF_RHS * np.sqrt(inner(CE, CE)))
         s = tan.apply(Ef + de)
         Ch[:, j] = to_comps(s.reshape(3, 3, -1).mean(axis=-1))
     return Ch

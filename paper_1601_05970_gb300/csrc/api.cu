@@ -91,7 +91,7 @@ namespace {
 enum : int {
     KK_CONSTITUTIVE_F32 = PK_COUNT, KK_CONSTITUTIVE_F64, KK_CG_UPDATE_F32, KK_CG_UPDATE_F64,
     KK_NEWTON_UPDATE_F32, KK_NEWTON_UPDATE_F64, KK_TANGENT_FLOOR, KK_TANGENT_AVERAGE,
-    KK_CG_FINISH_F32, KK_CG_FINISH_F64, KK_COUNT
+    KK_CG_FINISH_F32, KK_CG_FINISH_F64, KK_TANGENT_BOUNDS, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "p1_plain_f64", "p1_plain_f32", "p1_tan_f64", "p1_tan_f32", "p1_cg_f64", "p1_cg_f32",
@@ -99,7 +99,7 @@ const char* const kKindNames[KK_COUNT] = {
     "p5_plain_f64", "p5_plain_f32", "p5_dot_f64", "p5_dot_f32", "p5_rhs_f64_to_f64",
     "p5_rhs_f64_to_f32", "p5_rhs_f32_to_f32", "constitutive_f32", "constitutive_f64",
     "cg_update_f32", "cg_update_f64", "newton_update_f32", "newton_update_f64", "tangent_floor",
-    "tangent_average", "cg_finish_f32", "cg_finish_f64"};
+    "tangent_average", "cg_finish_f32", "cg_finish_f64", "tangent_bounds"};
 
 // Ring of event pairs around the handle's launches; drained at every read.
 struct Prof {
@@ -559,6 +559,33 @@ static fftg_handle::CgGraph* cg_graph_for(fftg_handle* h, int nf, const void* ta
     return &h->graphs.back();
 }
 
+// Basic scheme: the Richardson step of each of the nf CG states from the
+// extreme eigenvalues of the tangent(s), after the right-hand side pass.
+// ncells cells with nw states each (Newton: B cells x 1; tangent: 1 x 6).
+static int launch_bounds(fftg_handle* h, const void* tangent, long long cell_tangent, int ncells, int nw,
+                         const int* active) {
+    if (h->opt.solver != FFTG_SOLVER_RICHARDSON) return FFTG_OK;
+    VecArgs u{};
+    u.V = h->V;
+    u.cs = h->cs;
+    u.tangent = tangent;
+    u.cell_tangent = cell_tangent;
+    u.nw = nw;
+    u.cg = h->cg;
+    u.nd = h->nd;
+    u.partials = h->partials;
+    u.active = active;
+    const dim3 g(pointwise_blocks(h->V), ncells);
+    const int slot = prof_begin(h, KK_TANGENT_BOUNDS);
+    if (h->mixed)
+        k_tangent_bounds<float><<<g, kThreads, 0, h->stream>>>(u);
+    else
+        k_tangent_bounds<double><<<g, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    return FFTG_OK;
+}
+
 // x += alpha p for the solves whose last update left that step pending.
 static int launch_cg_finish(fftg_handle* h, int nf) {
     const bool f64 = !h->mixed;
@@ -651,6 +678,8 @@ int newton_round(fftg_handle* h, const int* run, double tol_inner, RoundOut* out
     int rc = launch_constitutive(h, h->active, B, 0, h->eps_work, h->sigma, false, h->cg);
     if (rc) return rc;
     rc = launch_residual(h);
+    if (rc) return rc;
+    rc = launch_bounds(h, h->tangent, 7 * h->cs, B, 1, h->active);
     if (rc) return rc;
     rc = run_cg(h, B, h->tangent, 7 * h->cs);
     if (rc) return rc;
@@ -906,7 +935,7 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     if (opt) o = *opt; else fftg_default_options(&o);
     if ((o.precision != FFTG_FP64 && o.precision != FFTG_MIXED) || o.max_newton < 1 || o.max_cg < 1 ||
         (o.nrhs_tangent != 0 && o.nrhs_tangent != 6) || o.fixed_cg < 0 || o.fixed_newton < 0 ||
-        !fftg::pos_finite(o.dt))
+        !fftg::pos_finite(o.dt) || (o.solver != FFTG_SOLVER_CG && o.solver != FFTG_SOLVER_RICHARDSON))
         return FFTG_EINVAL;
     for (int i = 0; i < nphase; ++i)
         if (!fftg::phase_valid(mats[i], true)) return FFTG_EINVAL;
@@ -1153,6 +1182,8 @@ int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters)
     b.cg = h->cg;
     CK(pass(h, f64 ? PK_P5_RHS_F64_TO_F64 : PK_P5_RHS_F32_TO_F32, b, 6));
     CK(cudaMemsetAsync(h->x, 0, 6 * 6 * h->cs * ts, h->stream));
+    rc = launch_bounds(h, tg, 0, 1, 6, nullptr);
+    if (rc) return rc;
     rc = run_cg(h, 6, tg, 0);
     if (rc) return rc;
     int total = 0;

@@ -37,6 +37,8 @@ struct CGState {
     double pq;       // <p, q>
     double alpha;
     double beta;
+    double omega;    // > 0: Richardson iteration with this fixed step (the
+                     // basic scheme, Section 3.4) instead of CG; 0: CG
     double rr_min;   // smallest <r, r> so far
     int it_min;      // iteration of rr_min
     int stag_window; // > 0: stagnation test window (set by the host)

@@ -650,6 +650,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 2) k
         cg->pend = 0;  // P1 of this iteration has added the previous step
         if (!isfinite(pq)) {
             cg->done = CG_BREAKDOWN;
+        } else if (cg->omega > 0.0) {
+            cg->alpha = cg->omega;  // Richardson: fixed step, <p, q> unused
         } else if (!(pq > 0.0)) {
             cg->done = cg->stag_window > 0 ? CG_STAGNATED : CG_BREAKDOWN;
         } else {

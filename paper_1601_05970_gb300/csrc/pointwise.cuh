@@ -272,6 +272,8 @@ struct VecArgs {
     double* out;       // tangent averages
     const int* active; // per cell (newton update): 0 = skip
     long long cell_fields;  // stride between cells of eps (newton update)
+    long long cell_tangent; // stride between cells of the tangent (bounds)
+    int nw;                 // CG states written per cell (bounds)
 };
 
 // r -= alpha q; rr = <r, r>; then beta, stopping test. The matching step
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
     const int it = cg->it + 1;
     cg->it = it;
     cg->pend = 1;
-    cg->beta = rr / cg->rr;
+    cg->beta = cg->omega > 0.0 ? 0.0 : rr / cg->rr;  // Richardson: p = r
     cg->rr = rr;
     if (!isfinite(rr)) {
         cg->done = CG_BREAKDOWN;
@@ -468,6 +470,85 @@ __global__ void __launch_bounds__(kThreads) k_tangent_average(VecArgs a) {
     reduce_partials<36>(a.partials, gridDim.x, &a.nd->ticket, tot);
     if (threadIdx.x == 0)
         for (int k = 0; k < 36; ++k) a.out[k] = tot[k];
+}
+
+// The basic scheme (Section 3.4, Moulinec-Suquet) solves the linear system
+// by Richardson's iteration with the reference medium
+// C_ref = (lambda_min + lambda_max)/2 I_s, lambda the extreme eigenvalues
+// of the local tangents over the grid; with Gamma_ref = G / c for
+// C_ref = c I_s (Appendix A), this is Richardson's iteration on G C with
+// the step omega = 2 / (lambda_min + lambda_max). On symmetric tensors with
+// the Frobenius product the compact tangent |K'| I(x)I + 2G_eff I_d + b N(x)N
+// has the eigenvalues 3|K'| (spherical), 2G_eff (deviatoric, orthogonal to
+// w) and 2G_eff - sign(K') |w|^2 (along w). The last block writes omega into
+// the nw CG states of the cell; it runs after the right-hand side pass (which
+// resets the states) and before the iteration.
+__device__ __forceinline__ void block_minmax(double& lo, double& hi) {
+    __shared__ double slo[kThreads / 32], shi[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        slo[wid] = lo;
+        shi[wid] = hi;
+    }
+    __syncthreads();
+    lo = slo[0];
+    hi = shi[0];
+    for (int k = 1; k < kThreads / 32; ++k) {
+        lo = fmin(lo, slo[k]);
+        hi = fmax(hi, shi[k]);
+    }
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(kThreads) k_tangent_bounds(VecArgs a) {
+    const int cell = blockIdx.y;
+    if (a.active && !a.active[cell]) return;
+    const long long V = a.V, cs = a.cs;
+    const TT* tg = (const TT*)a.tangent + cell * a.cell_tangent;
+    double lo = INFINITY, hi = -INFINITY;
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+        const double Kp = tg[v], g2 = tg[cs + v];
+        const double w0 = tg[2 * cs + v], w1 = tg[3 * cs + v], w3 = tg[4 * cs + v],
+                     w4 = tg[5 * cs + v], w5 = tg[6 * cs + v];
+        const double w2 = -(w0 + w1);
+        const double ww = w0 * w0 + w1 * w1 + w2 * w2 + 2.0 * (w3 * w3 + w4 * w4 + w5 * w5);
+        const double l1 = 3.0 * fabs(Kp), l3 = Kp < 0.0 ? g2 + ww : g2 - ww;
+        lo = fmin(lo, fmin(l1, fmin(g2, l3)));
+        hi = fmax(hi, fmax(l1, fmax(g2, l3)));
+    }
+    block_minmax(lo, hi);
+    double* partials = a.partials + (size_t)cell * gridDim.x * 2;
+    NewtonDev* nd = a.nd + cell;
+    const double part[2] = {lo, hi};
+    if (!publish_partials<2>(part, partials, blockIdx.x, gridDim.x, &nd->ticket)) return;
+    __threadfence();
+    lo = INFINITY;
+    hi = -INFINITY;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
+        lo = fmin(lo, __ldcg(partials + 2 * (size_t)b));
+        hi = fmax(hi, __ldcg(partials + 2 * (size_t)b + 1));
+    }
+    block_minmax(lo, hi);
+    if (threadIdx.x == 0) {
+        nd->ticket = 0u;
+        // the scheme needs positive definite tangents: otherwise the solve
+        // stops as a breakdown
+        const bool ok = lo > 0.0 && isfinite(hi);
+        for (int j = 0; j < a.nw; ++j) {
+            CGState& c = a.cg[cell * a.nw + j];
+            c.omega = ok ? 2.0 / (lo + hi) : 0.0;
+            if (!ok && c.done == CG_RUNNING) c.done = CG_BREAKDOWN;
+        }
+        nd->extra[0] = lo;
+        nd->extra[1] = hi;
+    }
 }
 
 }  // namespace fftg

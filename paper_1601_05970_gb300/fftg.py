@@ -25,6 +25,9 @@ FFTG_ECUDA = -6
 FFTG_ESTATE = -7
 FFTG_FP64 = 0
 FFTG_MIXED = 1
+FFTG_SOLVER_CG = 0
+FFTG_SOLVER_RICHARDSON = 1
+FFTG_MODEL_J2, FFTG_MODEL_NLELASTIC, FFTG_MODEL_VISCO = 0, 1, 2
 FFTG_FIELD_STRAIN = 0
 FFTG_FIELD_STRESS = 1
 FFTG_FIELD_EPBAR = 2
@@ -69,7 +72,8 @@ class fftg_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_newton", C.c_int), ("max_cg", C.c_int),
                 ("cg_inner_floor", C.c_double), ("fixed_cg", C.c_int), ("fixed_newton", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("nrhs_tangent", C.c_int), ("cg_graph", C.c_int), ("dt", C.c_double)]
+                ("nrhs_tangent", C.c_int), ("cg_graph", C.c_int), ("dt", C.c_double),
+                ("solver", C.c_int)]
 
 
 class fftg_result(C.Structure):
@@ -188,7 +192,7 @@ class Cell:
 
     def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
                  cg_inner_floor=1e-6, fixed_cg=0, fixed_newton=0, nrhs_tangent=6,
-                 device=None, stream=None, cg_graph=1, dt=1.0):
+                 device=None, stream=None, cg_graph=1, dt=1.0, solver="cg"):
         import torch
 
         lib = load()
@@ -206,6 +210,7 @@ class Cell:
         opt.nrhs_tangent = nrhs_tangent
         opt.cg_graph = cg_graph
         opt.dt = dt
+        opt.solver = {"cg": FFTG_SOLVER_CG, "richardson": FFTG_SOLVER_RICHARDSON}[solver]
         self.device = torch.device(device or "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opt.stream = C.c_void_p(self.stream.cuda_stream)
