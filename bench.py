@@ -236,6 +236,38 @@ def time_to_converged_stress(N, precisions=("mixed", "fp64"), n_inc=4, timed_fro
     return out
 
 
+def basic_scheme_line(N=135, n_inc=4, timed_from=2):
+    """The basic scheme of Section 3.4 (Richardson's iteration with the
+    reference medium (lambda_min + lambda_max)/2 I_s) against CG on the
+    same cell and load path: linear-solver iterations and wall time of the
+    plastic increments, mixed precision, fresh cells (no tangent)."""
+    import torch
+    from paper_1601_05970_gb300 import fftg
+    from paper_1601_05970_gb300 import inputs as I
+    w = I.workload("spheres135")
+    out = {"N": N, "workload": "spheres135-uniaxial", "precision": "mixed"}
+    for solver in ("cg", "richardson"):
+        cell = fftg.Cell(N, w["phase"], w["mats"], precision="mixed", nrhs_tangent=0,
+                         solver=solver, max_cg=20000)
+        t_tot, iters = 0.0, []
+        for k in range(n_inc):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sig, nn, nc = cell.step(w["dE"][k], w["tol_newton"], w["tol_cg"])
+            torch.cuda.synchronize()
+            if k >= timed_from:
+                t_tot += time.perf_counter() - t0
+                iters.append((nn, nc))
+        out[solver] = dict(seconds=t_tot, newton_iters=[a for a, _ in iters],
+                           solver_iters=[b for _, b in iters], sigma=[float(v) for v in sig])
+        cell.close()
+        del cell
+        torch.cuda.empty_cache()
+    out["iteration_ratio"] = sum(out["richardson"]["solver_iters"]) / max(1, sum(out["cg"]["solver_iters"]))
+    out["time_ratio"] = out["richardson"]["seconds"] / out["cg"]["seconds"]
+    return out
+
+
 def cufft_matvec_line(N, iters=10):
     """Comparison line: q = G(C:p) with library FFTs (cuFFT through
     torch.fft rfftn/irfftn, FP32) and separate elementwise kernels for C:p
@@ -428,6 +460,7 @@ def main():
                                       "separate elementwise C:p and Ghat kernels, vs the fused passes "
                                       "P1-P5 per CG field-iteration in the timed region"}
         line["time_to_converged_stress"] = time_to_converged_stress(N)
+        line["basic_scheme_vs_cg"] = basic_scheme_line()
         rves = serving.batched_workload()
         line["batched"] = serving.run_batched(rves)
         line["serving"] = serving.run(args.serve_rate, args.serve_seconds, budget_gb=48.0)
