@@ -100,7 +100,7 @@ typedef struct {
     int    max_newton;      /* Newton iteration cap per increment (default 50) */
     int    max_cg;          /* CG iteration cap per solve (default 2000) */
     double cg_inner_floor;  /* FFTG_MIXED: the FP32 CG tolerance is
-                               max(tol_cg, cg_inner_floor) (default 1e-6) */
+                               max(tol_cg, cg_inner_floor) (default 1e-5) */
     int    fixed_cg;        /* > 0: every CG solve runs exactly this many
                                iterations (parity mode); 0 = off */
     int    fixed_newton;    /* > 0: every increment runs exactly this many

@@ -559,6 +559,35 @@ static fftg_handle::CgGraph* cg_graph_for(fftg_handle* h, int nf, const void* ta
     return &h->graphs.back();
 }
 
+// Mixed precision: x <- G x (FP32 passes) on the nf solution fields. The
+// FP32 recursion of CG lets the residual, and with it x, drift out of the
+// compatible space (by about 1e-5 of |x| over some tens of iterations:
+// each q = G (C : p) carries FP32 rounding). Newton's corrections then add
+// an incompatible part to eps* that no later correction removes, and the
+// converged state sits off the FP64 solution by that much. One projection
+// per solve brings the incompatible part down to the rounding of a single
+// FP32 projection.
+#ifndef FFTG_PROJECT_X
+#define FFTG_PROJECT_X 1
+#endif
+static int project_solution(fftg_handle* h, int nf, const int* active) {
+    if (!h->mixed || !FFTG_PROJECT_X) return FFTG_OK;
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    PassArgs a = base_args(h, false);
+    a.in = h->x;
+    a.out = h->spec;
+    a.active = active;
+    CK(pass(h, PK_P1_PLAIN_F32, a, nf));
+    int rc = run_p234(h, false, invN3, nullptr, nf, active);
+    if (rc) return rc;
+    PassArgs b = base_args(h, false);
+    b.in = h->spec;
+    b.out = h->x;
+    b.active = active;
+    CK(pass(h, PK_P5_PLAIN_F32, b, nf));
+    return FFTG_OK;
+}
+
 // Basic scheme: the Richardson step of each of the nf CG states from the
 // extreme eigenvalues of the tangent(s), after the right-hand side pass.
 // ncells cells with nw states each (Newton: B cells x 1; tangent: 1 x 6).
@@ -682,6 +711,8 @@ int newton_round(fftg_handle* h, const int* run, double tol_inner, RoundOut* out
     rc = launch_bounds(h, h->tangent, 7 * h->cs, B, 1, h->active);
     if (rc) return rc;
     rc = run_cg(h, B, h->tangent, 7 * h->cs);
+    if (rc) return rc;
+    rc = project_solution(h, B, h->active);
     if (rc) return rc;
     VecArgs u{};
     u.V = h->V;
@@ -905,7 +936,7 @@ void fftg_default_options(fftg_options* o) {
     o->precision = FFTG_MIXED;
     o->max_newton = 50;
     o->max_cg = 2000;
-    o->cg_inner_floor = 1e-6;
+    o->cg_inner_floor = 1e-5;
     o->nrhs_tangent = 6;
     o->cg_graph = 1;
     o->dt = 1.0;
@@ -1185,6 +1216,8 @@ int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters)
     rc = launch_bounds(h, tg, 0, 1, 6, nullptr);
     if (rc) return rc;
     rc = run_cg(h, 6, tg, 0);
+    if (rc) return rc;
+    rc = project_solution(h, 6, nullptr);
     if (rc) return rc;
     int total = 0;
     for (int f = 0; f < 6; ++f) {

@@ -191,7 +191,7 @@ class Cell:
     """
 
     def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
-                 cg_inner_floor=1e-6, fixed_cg=0, fixed_newton=0, nrhs_tangent=6,
+                 cg_inner_floor=1e-5, fixed_cg=0, fixed_newton=0, nrhs_tangent=6,
                  device=None, stream=None, cg_graph=1, dt=1.0, solver="cg"):
         import torch
 
@@ -365,7 +365,7 @@ class Server:
     """
 
     def __init__(self, N, slots, mats, precision="mixed", tol_newton=1e-5, tol_cg=1e-8,
-                 max_newton=50, max_cg=2000, cg_inner_floor=1e-6, cg_graph=1, dt=1.0):
+                 max_newton=50, max_cg=2000, cg_inner_floor=1e-5, cg_graph=1, dt=1.0):
         lib = load()
         self.N = int(N)
         opt = default_options()
