@@ -60,6 +60,22 @@ def bytes_per_voxel(N):
     }
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the dominant kernel from one ncu capture (profiles/traffic_cg_kernels_
+# spheres243.md), valid while the kernel sources have the digest they had
+# then (SHA-256 prefix of csrc/common.cuh + fft_core.cuh + passes.cuh).
+TRAFFIC = {"p1_cg_f32": {"N": 243, "bytes": 2417.8e6, "digest": "a092d4a63a450e6d"}}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("common.cuh", "fft_core.cuh", "passes.cuh"):
+        with open(os.path.join(ROOT, "paper_1601_05970_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,8 +435,10 @@ def main():
         alg_bytes = eff[kind] * V * bpv[kind]
         achieved = alg_bytes / (kms * 1e-3) / 1e9
         per_launch = alg_bytes / max(eff[kind], 1)
+        tr = TRAFFIC.get(kind)
+        traffic = tr["bytes"] if tr and tr["N"] == N and tr["digest"] == kernel_digest() else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": kind,
+                "frac": achieved / hbm, "traffic": traffic, "kernel": kind,
                 "peak_source": peak_kind, "bytes_per_launch": per_launch,
                 "avg_launch_ms": kms / max(eff[kind], 1)}
     line = {
