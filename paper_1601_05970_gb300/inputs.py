@@ -123,9 +123,27 @@ def material_tuple(m):
 # The two-phase material set used by every workload: bulk 0.833, shear 0.386,
 # soft matrix (phase 0) yield 0.003 / hardening 0.01, hard phase (phase 1)
 # yield 0.006 / hardening 0.02 (yield and hardening ratio 2 as in Section 5.2).
+@dataclass(frozen=True)
+class SaintVenantKirchhoff:
+    """Hyperelastic phase of the finite-strain path: W = lambda/2 (tr E)^2
+    + mu E : E with the Green-Lagrange strain E = (F^T F - I)/2. Its
+    small-strain limit is isotropic elasticity with K = lambda + 2 mu/3,
+    G = mu."""
+
+    lam: float
+    mu: float
+
+    def as_tuple(self):
+        return (self.lam, self.mu)
+
+
 SOFT = Phase(K=0.833, G=0.386, sigma_y=0.003, H=0.01)
 HARD = Phase(K=0.833, G=0.386, sigma_y=0.006, H=0.02)
 TWO_PHASE = (SOFT, HARD)
+# Finite strain: the elastic constants of SOFT and a phase five times stiffer
+SVK_SOFT = SaintVenantKirchhoff(lam=0.833 - 2.0 * 0.386 / 3.0, mu=0.386)
+SVK_HARD = SaintVenantKirchhoff(lam=5.0 * (0.833 - 2.0 * 0.386 / 3.0), mu=5.0 * 0.386)
+SVK_TWO_PHASE = (SVK_SOFT, SVK_HARD)
 
 
 def check_grid(N: int) -> None:
