@@ -284,6 +284,75 @@ def basic_scheme_line(N=135, n_inc=4, timed_from=2):
     return out
 
 
+def fs_bytes_per_voxel(N):
+    """Algorithmic bytes per voxel of the finite-strain CG kernels (FP32
+    fields of nine components, 36 B per voxel; half spectrum 9 x (H/N) x 8 B;
+    the tangent data is H = F - I, 36 B, and the phase byte)."""
+    H = (N + 1) // 2
+    s32 = 9 * 8 * H / N
+    return {"fs_p1_cg_f32": 5 * 36 + 36 + 1 + s32,
+            "fs_p2_f32": 2 * s32, "fs_p3_f32": 2 * s32, "fs_p4_f32": 2 * s32,
+            "fs_p5_dot_f32": s32 + 36 + 36, "fs_cg_update_f32": 3 * 36}
+
+
+def finite_strain_line(warm=1, timed=2):
+    """The finite-strain extension (St. Venant-Kirchhoff, first
+    Piola-Kirchhoff stress, gradient projection) on the 243^3 spheres cell,
+    mixed precision: increments warm.. of the stretch-shear path timed with
+    CUDA events and per-kernel events, the roofline of its dominant kernel."""
+    import torch
+    from paper_1601_05970_gb300 import fftg
+    from paper_1601_05970_gb300 import inputs as I
+    w = I.workload("fs_spheres243")
+    N = w["N"]
+    V = N ** 3
+    cell = fftg.FsCell(N, w["phase"], w["mats"], precision="mixed")
+    for k in range(warm):
+        cell.step(w["dF"][k], w["tol_newton"], w["tol_cg"])
+    cell.profile(True)
+    stream = cell.stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = cell.launches()
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    nn_tot = nc_tot = 0
+    for k in range(warm, warm + timed):
+        P, nn, nc = cell.step(w["dF"][k], w["tol_newton"], w["tol_cg"])
+        nn_tot += nn
+        nc_tot += nc
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev_ms = ev0.elapsed_time(ev1)
+    prof = cell.profile_read()
+    launches = cell.launches() - l0
+    cell.close()
+    del cell
+    torch.cuda.empty_cache()
+    bpv = fs_bytes_per_voxel(N)
+    eff = {"fs_p1_cg_f32": nc_tot, "fs_p5_dot_f32": nc_tot, "fs_cg_update_f32": nc_tot,
+           "fs_p2_f32": nc_tot + nn_tot, "fs_p3_f32": nc_tot + nn_tot, "fs_p4_f32": nc_tot + nn_tot}
+    kind, (kms, kn) = max(((k, v) for k, v in prof.items() if k in bpv), key=lambda kv: kv[1][0])
+    hbm, peak_kind = measured_hbm()
+    alg = eff[kind] * V * bpv[kind]
+    achieved = alg / (kms * 1e-3) / 1e9
+    return {
+        "metric": "CG-iter voxels/s at 243^3, finite strain (FP32-inner mixed precision)",
+        "value": V * nc_tot / (dev_ms * 1e-3), "unit": UNIT,
+        "e2e_value": V * nc_tot / wall, "workload": "fs_spheres243-stretch-shear",
+        "increments_timed": timed, "newton_iters": nn_tot, "cg_iters": nc_tot,
+        "P": [float(v) for v in P.reshape(-1)], "ms": dev_ms, "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": kind,
+                     "peak_source": peak_kind, "bytes_per_launch": alg / max(eff[kind], 1),
+                     "avg_launch_ms": kms / max(eff[kind], 1)},
+        "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in sorted(
+            prof.items(), key=lambda kv: -kv[1][0])},
+    }
+
+
 def cufft_matvec_line(N, iters=10):
     """Comparison line: q = G(C:p) with library FFTs (cuFFT through
     torch.fft rfftn/irfftn, FP32) and separate elementwise kernels for C:p
@@ -479,6 +548,7 @@ def main():
                                       "P1-P5 per CG field-iteration in the timed region"}
         line["time_to_converged_stress"] = time_to_converged_stress(N)
         line["basic_scheme_vs_cg"] = basic_scheme_line()
+        line["finite_strain"] = finite_strain_line()
         rves = serving.batched_workload()
         line["batched"] = serving.run_batched(rves)
         line["serving"] = serving.run(args.serve_rate, args.serve_seconds, budget_gb=48.0)

@@ -11,7 +11,8 @@
  * for the compatible fluctuation eps* by the incremental Newton-CG scheme of
  * Algorithm 1, with the J2 elasto-plastic law of Section 4.2 (linear
  * isotropic hardening), and returns the homogenised stress (Eq. trapz: the
- * nodal mean of sigma).
+ * nodal mean of sigma). The finite-strain extension (deformation gradient,
+ * first Piola-Kirchhoff stress) is declared in fftg_fs.h.
  *
  * Conventions shared by every entry point:
  *  - A symmetric tensor is 6 doubles in the order (11, 22, 33, 23, 13, 12),

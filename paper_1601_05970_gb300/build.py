@@ -1,7 +1,8 @@
 """Build libfftg.so in-tree with nvcc for sm_103a.
 
-The pass kernels are compiled once per supported grid size, in parallel, and
-linked with the host driver into one shared library next to this file.
+The pass kernels (small and finite strain) are compiled once per supported
+grid size, in parallel, and linked with the host drivers into one shared
+library next to this file.
 """
 from __future__ import annotations
 
@@ -64,6 +65,11 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         units.append(([nvcc] + ARCH + FLAGS + [f"-DFFTG_N={n}", "-c",
                        os.path.join(CSRC, "passes_inst.cu"), "-o",
                        os.path.join(BUILD, f"passes_{n}.o")]))
+        units.append(([nvcc] + ARCH + FLAGS + [f"-DFFTG_N={n}", "-c",
+                       os.path.join(CSRC, "fs_inst.cu"), "-o",
+                       os.path.join(BUILD, f"fs_{n}.o")]))
+    units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "finite_strain.cu"), "-o",
+                                          os.path.join(BUILD, "finite_strain.o")])
     units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "api.cu"), "-o",
                                           os.path.join(BUILD, "api.o")])
     units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "noalloc.cu"), "-o",
@@ -75,7 +81,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         for out in ex.map(_run, units):
             logs.append(out)
     objs = ([os.path.join(BUILD, f"passes_{n}.o") for n in GRIDS]
-            + [os.path.join(BUILD, "api.o"), os.path.join(BUILD, "noalloc.o"),
+            + [os.path.join(BUILD, f"fs_{n}.o") for n in GRIDS]
+            + [os.path.join(BUILD, "finite_strain.o"), os.path.join(BUILD, "api.o"), os.path.join(BUILD, "noalloc.o"),
                os.path.join(BUILD, "server.o")])
     tmp = LIB + ".tmp"
     _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])

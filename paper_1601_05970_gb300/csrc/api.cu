@@ -17,6 +17,7 @@
 
 #include "../../include/fftg.h"
 #include "driver.h"
+#include "host_common.h"
 #include "materials.h"
 #include "passes.cuh"
 #include "pointwise.cuh"
@@ -38,15 +39,7 @@ FFTG_EXTERN_N(225)
 FFTG_EXTERN_N(243)
 #undef FFTG_EXTERN_N
 
-static bool supported_n(int N) {
-    switch (N) {
-        case 3: case 5: case 9: case 15: case 25: case 27: case 45: case 75: case 81: case 125:
-        case 135: case 225: case 243:
-            return true;
-        default:
-            return false;
-    }
-}
+static bool supported_n(int N) { return supported_grid(N); }
 
 cudaError_t run_pass(int N, PassKind kind, const PassArgs& a, int nf, cudaStream_t s) {
     switch (N) {
@@ -230,14 +223,6 @@ namespace {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Component stride of every field: N^3 rounded up past N^3 + 4 to a
-// multiple of 32 elements, so each component starts 128-byte aligned and a
-// 16-byte vector that straddles the end of the grid stays in the padding.
-long long comp_stride(int N) {
-    const long long V = (long long)N * N * N;
-    return ((V + 4 + 31) / 32) * 32;
-}
-
 struct Layout {
     size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p, off_eps_p_tr, off_epbar,
         off_epbar_tr, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32,
@@ -301,19 +286,6 @@ bool valid_grid(int N) {
 double frob6(const double* v) {
     return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] +
                      2.0 * (v[3] * v[3] + v[4] * v[4] + v[5] * v[5]));
-}
-
-// w_N^j = exp(-2 pi i j / N), evaluated in long double on the host.
-void twiddles(int N, double* tw64, float* tw32) {
-    const long double two_pi = 6.283185307179586476925286766559L;
-    for (int j = 0; j < N; ++j) {
-        const long double a = two_pi * (long double)j / (long double)N;
-        const double c = (double)cosl(a), s = (double)-sinl(a);
-        tw64[2 * j] = c;
-        tw64[2 * j + 1] = s;
-        tw32[2 * j] = (float)c;
-        tw32[2 * j + 1] = (float)s;
-    }
 }
 
 }  // namespace

@@ -61,6 +61,75 @@ struct NewtonDev {
     int nplastic;     // unused slot kept for alignment
 };
 
+// Transitions of a CGState, taken by thread 0 of the last block of a
+// reducing kernel once the block totals are in.
+//
+// Start of a solve, after the right-hand side pass: rr = <r0, r0> in the
+// inner precision, gs2 = ||G sigma||^2 before rounding to it.
+__device__ __forceinline__ void cg_start(CGState* cg, double rr, double gs2) {
+    cg->rr = rr;
+    cg->rr0 = rr;
+    cg->rr_min = rr;
+    cg->it_min = 0;
+    cg->gs2 = gs2;
+    cg->it = 0;
+    cg->beta = 0.0;
+    cg->alpha = 0.0;
+    const double stop2 = fmax(cg->tol2 * rr, cg->floor2);
+    cg->stop2 = stop2;
+    if (!isfinite(rr) || !isfinite(gs2)) {
+        cg->done = CG_BREAKDOWN;
+    } else if (gs2 <= cg->floor2 || rr == 0.0) {
+        cg->done = CG_CONVERGED;
+    } else if (cg->fixed_it <= 0 && rr <= stop2) {
+        cg->done = CG_CONVERGED;
+    } else {
+        cg->done = CG_RUNNING;
+    }
+}
+
+// After the matvec of an iteration: alpha = <r, r>/<p, q>, or the fixed
+// Richardson step.
+__device__ __forceinline__ void cg_after_dot(CGState* cg, double pq) {
+    cg->pq = pq;
+    cg->pend = 0;  // P1 of this iteration has added the previous step
+    if (!isfinite(pq)) {
+        cg->done = CG_BREAKDOWN;
+    } else if (cg->omega > 0.0) {
+        cg->alpha = cg->omega;  // Richardson: fixed step, <p, q> unused
+    } else if (!(pq > 0.0)) {
+        cg->done = cg->stag_window > 0 ? CG_STAGNATED : CG_BREAKDOWN;
+    } else {
+        cg->alpha = cg->rr / pq;
+    }
+}
+
+// After r -= alpha q: rr = <r, r>; beta and the stopping tests. The step
+// x += alpha p is left pending.
+__device__ __forceinline__ void cg_after_update(CGState* cg, double rr) {
+    const int it = cg->it + 1;
+    cg->it = it;
+    cg->pend = 1;
+    cg->beta = cg->omega > 0.0 ? 0.0 : rr / cg->rr;  // Richardson: p = r
+    cg->rr = rr;
+    if (!isfinite(rr)) {
+        cg->done = CG_BREAKDOWN;
+    } else if (cg->fixed_it > 0) {
+        if (it >= cg->fixed_it) cg->done = CG_CONVERGED;
+    } else if (rr <= cg->stop2) {
+        cg->done = CG_CONVERGED;
+    } else if (it >= cg->max_it) {
+        cg->done = CG_MAXIT;
+    } else if (cg->stag_window > 0) {
+        if (rr < cg->rr_min) {
+            cg->rr_min = rr;
+            cg->it_min = it;
+        } else if (it - cg->it_min >= cg->stag_window) {
+            cg->done = CG_STAGNATED;
+        }
+    }
+}
+
 // Frobenius product of symmetric tensors stored as 6 components
 template <typename T>
 __device__ __forceinline__ T frob(const T* a, const T* b) {

@@ -1,0 +1,457 @@
+// Grid passes of the finite-strain extension (Section 6 names finite strain
+// as the next step of the method): the projected matvec q = G (K : p) and
+// the residual G P on real fields of nine components, the deformation-
+// gradient-like tensor A_ij at component 3i + j, [9][cs], and a half
+// spectrum [9][N][N][H].
+//
+// The five passes are those of the small-strain path with two changes:
+//  * nine real components share five complex FFTs per row (pairs (0,1),
+//    (2,3), (4,5), (6,7) and component 8 alone);
+//  * the projection onto gradient fields acts row by row: with n = xi/|xi|,
+//    Ghat : A = (A n) (x) n, i.e. Ghat_ijlm = delta_il n_j n_m (the
+//    finite-strain counterpart of Appendix A's operator; Ghat(0) = 0);
+//  * the tangent is St. Venant-Kirchhoff's, applied on the fly from the
+//    displacement gradient H = F - I (the only per-voxel tangent data) and
+//    the phase's Lame constants: K : d = d S + F dS with
+//    E = (H + H^T + H^T H)/2, S = lambda tr(E) I + 2 mu E, M = F^T d and
+//    dS = lambda tr(M) I + mu (M + M^T).
+#pragma once
+
+#include "common.cuh"
+#include "fft_core.cuh"
+#include "passes.cuh"
+
+namespace fftg {
+
+constexpr int kFsComp = 9;
+constexpr int kFsPairs = 5;
+
+enum : int { FS_P1_PLAIN = 0, FS_P1_TAN = 1, FS_P1_CG = 2 };
+enum : int { FS_P5_PLAIN = 0, FS_P5_DOT = 1, FS_P5_RHS = 2 };
+
+struct FsArgs {
+    const void* in;        // P1: real field; P5: spectrum
+    void* out;             // P1: spectrum; P2-P4: spectrum (in place); P5: real field
+    const void* aux;       // P1_CG: r; P5_DOT: p
+    void* aux2;            // P1_CG: p (updated in place)
+    void* aux3;            // P1_CG: x (gets the previous iteration's alpha p)
+    const void* hgrad;     // P1_TAN, P1_CG: H = F - I, [9][cs] in the FFT precision
+    const uint8_t* phase;  // [cs]
+    const double* lame;    // [nphase][2]: lambda, mu
+    CGState* cg;
+    double* partials;      // [row blocks][2]
+    const void* tw;        // w_N^j, j < N, in the FFT precision
+    double scale;          // P3: factor on Ghat (+-1/N^3)
+    long long cs;          // component stride of the real fields (elements)
+};
+
+template <int N, typename T>
+struct FsCfg {
+    static constexpr int H = (N + 1) / 2;
+    static constexpr int CS = (int)sizeof(cplx<T>);
+    static constexpr int fl2(int x) {
+        return x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1;
+    }
+    static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
+    static constexpr int cap(int x) { return x > 1024 ? 1024 : x; }
+    // rows per block of P1/P5: five complex pencils per row in ~80 KB
+    static constexpr int R = fl2(80 * 1024 / (kFsPairs * N * CS));
+    // columns per block of P3: nine pencils per column in ~150 KB
+    static constexpr int W3 = fl2(150 * 1024 / (kFsComp * N * CS));
+    static constexpr int T3 = Plan<N>::N2 == 1 ? 256 : cap(rup32(kFsComp * W3 * Plan<N>::N2));
+    static constexpr size_t smem_rows = (size_t)(kFsPairs * R * N + N) * CS;
+    static constexpr size_t smem_p3 = (size_t)(kFsComp * W3 * N + N) * CS;
+    static constexpr int row_blocks = (N * N + R - 1) / R;
+    static_assert(smem_rows <= 227 * 1024 && smem_p3 <= 227 * 1024, "shared memory per block");
+    static_assert(T3 <= 1024 && T3 % 32 == 0, "threads per block");
+};
+
+// tau = K(F) : d for St. Venant-Kirchhoff, from h = F - I.
+template <typename T>
+__device__ __forceinline__ void svk_tangent_apply(const T (&h)[9], T lam, T mu, const T (&d)[9], T (&tau)[9]) {
+    T E[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T hh = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) hh += h[3 * k + i] * h[3 * k + j];
+            E[3 * i + j] = T(0.5) * (h[3 * i + j] + h[3 * j + i] + hh);
+        }
+    const T le = lam * (E[0] + E[4] + E[8]);
+    T M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T m = d[3 * i + j];  // (I + H)^T d
+#pragma unroll
+            for (int k = 0; k < 3; ++k) m += h[3 * k + i] * d[3 * k + j];
+            M[3 * i + j] = m;
+        }
+    const T lm = lam * (M[0] + M[4] + M[8]);
+    T S[9], dS[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            S[3 * i + j] = T(2) * mu * E[3 * i + j] + (i == j ? le : T(0));
+            dS[3 * i + j] = mu * (M[3 * i + j] + M[3 * j + i]) + (i == j ? lm : T(0));
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T t = dS[3 * i + j];  // I dS
+#pragma unroll
+            for (int k = 0; k < 3; ++k) t += d[3 * i + k] * S[3 * k + j] + h[3 * i + k] * dS[3 * k + j];
+            tau[3 * i + j] = t;
+        }
+}
+
+// ----------------------------------------------------------------------- P1
+// [x += alpha p; p = r + beta p]; tau = K : p or tau = input; x3 R2C FFT of
+// R rows per block.
+template <int N, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_fs_p1(FsArgs a) {
+    using C = FsCfg<N, T>;
+    constexpr int R = C::R, H = C::H;
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* z = tw + N;  // [5][R][N]
+    if (MODE == FS_P1_CG && a.cg->done) return;
+    const int tid = threadIdx.x;
+    load_tw<T>(tw, a.tw, N);
+    const int row0 = blockIdx.x * R;
+    const int nrows = min(R, N * N - row0);
+    const long long base = (long long)row0 * N;
+    const int nel = nrows * N;
+    const long long cs = a.cs;
+    T beta = T(0), alpha = T(0);
+    bool first = true;
+    if (MODE == FS_P1_CG) {
+        beta = (T)a.cg->beta;
+        alpha = (T)a.cg->alpha;
+        first = a.cg->it == 0;
+    }
+    for (int i = tid; i < R * N; i += kThreads) {
+        T s[9];
+        if (i < nel) {
+            const long long v = base + i;
+            T p[9];
+            if (MODE == FS_P1_CG) {
+                const T* r = (const T*)a.aux;
+                T* pp = (T*)a.aux2;
+                T* xx = (T*)a.aux3;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    p[c] = r[c * cs + v];
+                    if (!first) {
+                        const T po = pp[c * cs + v];
+                        xx[c * cs + v] += alpha * po;
+                        p[c] += beta * po;
+                    }
+                    pp[c * cs + v] = p[c];
+                }
+            } else {
+                const T* in = (const T*)a.in;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) p[c] = in[c * cs + v];
+            }
+            if (MODE == FS_P1_PLAIN) {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) s[c] = p[c];
+            } else {
+                const T* hg = (const T*)a.hgrad;
+                T h[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) h[c] = hg[c * cs + v];
+                const double* m = a.lame + 2 * a.phase[v];
+                svk_tangent_apply<T>(h, (T)m[0], (T)m[1], p, s);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) s[c] = T(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) z[c * R * N + i] = mk(s[2 * c], s[2 * c + 1]);
+        z[4 * R * N + i] = mk(s[8], T(0));
+    }
+    __syncthreads();
+    constexpr int NP = kFsPairs * R;
+    for (int it = tid; it < NP * N2; it += kThreads) {
+        const int pc = it % NP, t = it / NP;
+        if (pc % R < nrows) fwdA<N, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
+    }
+    __syncthreads();
+    if (N2 > 1) {
+        for (int it = tid; it < NP * N1; it += kThreads) {
+            const int pc = it % NP, k1 = it / NP;
+            if (pc % R < nrows) fwdB<N, false, T>(z + pc * N, 1, z + pc * N, 1, k1, tw);
+        }
+        __syncthreads();
+    }
+    // Split each packed transform Z = FFT(a + i b) into the half spectra
+    // A_k = (Z_k + conj Z_{N-k})/2 and B_k = (Z_k - conj Z_{N-k})/(2i).
+    cplx<T>* out = (cplx<T>*)a.out;
+    const long long HS = (long long)N * N * H;
+    for (int it = tid; it < nrows * H; it += kThreads) {
+        const int row = it / H, k = it - row * H;
+        const int pk = perm_pos<N>(k), pn = perm_pos<N>(k == 0 ? 0 : N - k);
+        const long long o = (long long)(row0 + row) * H + k;
+#pragma unroll
+        for (int c = 0; c < kFsPairs; ++c) {
+            const cplx<T> zk = z[(c * R + row) * N + pk];
+            const cplx<T> zn = conj(z[(c * R + row) * N + pn]);
+            out[(2 * c) * HS + o] = T(0.5) * (zk + zn);
+            if (2 * c + 1 < kFsComp) {
+                const cplx<T> d = zk - zn;
+                out[(2 * c + 1) * HS + o] = mk(T(0.5) * d.y, T(-0.5) * d.x);
+            }
+        }
+    }
+}
+
+// Ghat_fs : A at frequency (f1, f2, f3), times `scale`, in place on the nine
+// complex components held at stride `cs`: row i becomes (A_i . n) n.
+template <typename T>
+__device__ __forceinline__ void ghat_fs_point(cplx<T>* b, int cs, int f1, int f2, int f3, T scale) {
+    const T q2 = T(f1) * T(f1) + T(f2) * T(f2) + T(f3) * T(f3);
+    const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
+    const T n0 = T(f1) * inv, n1 = T(f2) * inv, n2 = T(f3) * inv;
+    const T m0 = scale * n0, m1 = scale * n1, m2 = scale * n2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const cplx<T> t = n0 * b[(3 * i) * cs] + n1 * b[(3 * i + 1) * cs] + n2 * b[(3 * i + 2) * cs];
+        b[(3 * i) * cs] = m0 * t;
+        b[(3 * i + 1) * cs] = m1 * t;
+        b[(3 * i + 2) * cs] = m2 * t;
+    }
+}
+
+// ------------------------------------------------------------- P3 (x1 + Ghat)
+// As the small-strain P3: stage A forward into shared memory, stage B
+// forward in place, Ghat_fs with one thread per (column, frequency), stage B
+// inverse, stage A inverse back to the spectrum.
+template <int N, typename T>
+__global__ void __launch_bounds__(FsCfg<N, T>::T3) k_fs_p3(FsArgs a) {
+    using C = FsCfg<N, T>;
+    constexpr int H = C::H, W = C::W3, NT = C::T3;
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf = tw + N;  // [9][N][W]
+    if (a.cg && a.cg->done) return;
+    const int tid = threadIdx.x;
+    load_tw<T>(tw, a.tw, N);
+    __syncthreads();
+    const int col0 = blockIdx.x * W, k2g = blockIdx.y;
+    cplx<T>* sp = (cplx<T>*)a.out;
+    constexpr int P = kFsComp * W;
+    const long long NH = (long long)N * H;
+    for (int it = tid; it < P * N2; it += NT) {
+        const int pc = it % P, t = it / P;
+        const int c = pc / W, w = pc - c * W, col = col0 + w;
+        if (col < H) fwdA<N, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
+    }
+    __syncthreads();
+    const T scale = (T)a.scale;
+    const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
+    if (N2 > 1) {
+        for (int it = tid; it < P * N1; it += NT) {
+            const int pc = it % P, k1 = it / P;
+            const int c = pc / W, w = pc - c * W;
+            if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+        }
+        __syncthreads();
+    }
+    for (int it = tid; it < W * N; it += NT) {
+        const int w = it % W, pos = it / W, col = col0 + w;
+        const int k1 = pos / N2, k2 = pos - k1 * N2;
+        const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
+        if (col < H)
+            ghat_fs_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
+    }
+    __syncthreads();
+    if (N2 > 1) {
+        for (int it = tid; it < P * N1; it += NT) {
+            const int pc = it % P, k1 = it / P;
+            const int c = pc / W, w = pc - c * W;
+            if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+        }
+    }
+    __syncthreads();
+    for (int it = tid; it < P * N2; it += NT) {
+        const int pc = it % P, t = it / P;
+        const int c = pc / W, w = pc - c * W, col = col0 + w;
+        if (col < H) invA<N, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, t, tw);
+    }
+}
+
+// ----------------------------------------------------------------------- P5
+// x3 C2R inverse FFT of R rows per block; writes the real field (in TO) and,
+// for DOT, the partials of <p, q> (then alpha), for RHS those of <r, r> in
+// TO and of ||G P||^2 in T (then the start of the CG solve).
+template <int N, typename T, int MODE, typename TO>
+__global__ void __launch_bounds__(kThreads) k_fs_p5(FsArgs a) {
+    using C = FsCfg<N, T>;
+    constexpr int R = C::R, H = C::H;
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* z = tw + N;  // [5][R][N]
+    CGState* cg = a.cg;
+    if (MODE == FS_P5_DOT && cg->done) return;
+    const int tid = threadIdx.x;
+    load_tw<T>(tw, a.tw, N);
+    const int row0 = blockIdx.x * R;
+    const int nrows = min(R, N * N - row0);
+    const long long base = (long long)row0 * N;
+    const int nel = nrows * N;
+    const cplx<T>* in = (const cplx<T>*)a.in;
+    const long long HS = (long long)N * N * H;
+    for (int it = tid; it < nrows * H; it += kThreads) {
+        const int row = it / H, k = it - row * H;
+        const long long o = (long long)(row0 + row) * H + k;
+        const int pk = perm_pos<N>(k);
+        const int pn = perm_pos<N>(k == 0 ? 0 : N - k);
+#pragma unroll
+        for (int c = 0; c < kFsPairs; ++c) {
+            const cplx<T> a0 = in[(2 * c) * HS + o];
+            const cplx<T> b0 = (2 * c + 1 < kFsComp) ? in[(2 * c + 1) * HS + o] : mk(T(0), T(0));
+            z[(c * R + row) * N + pk] = mk(a0.x - b0.y, a0.y + b0.x);                  // A + iB
+            if (k > 0) z[(c * R + row) * N + pn] = mk(a0.x + b0.y, b0.x - a0.y);  // conj(A) + i conj(B)
+        }
+    }
+    __syncthreads();
+    constexpr int NP = kFsPairs * R;
+    if (N2 > 1) {
+        for (int it = tid; it < NP * N1; it += kThreads) {
+            const int pc = it % NP, k1 = it / NP;
+            if (pc % R < nrows) invB<N, false, T>(z + pc * N, 1, z + pc * N, 1, k1, tw);
+        }
+        __syncthreads();
+    }
+    for (int it = tid; it < NP * N2; it += kThreads) {
+        const int pc = it % NP, t = it / NP;
+        if (pc % R < nrows) invA<N, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
+    }
+    __syncthreads();
+    const long long cs = a.cs;
+    TO* out = (TO*)a.out;
+    const TO* pin = (const TO*)a.aux;
+    T acc0 = T(0);
+    double acc1 = 0.0;
+    for (int i = tid; i < nel; i += kThreads) {
+        const long long v = base + i;
+        T qd[9];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const cplx<T> zz = z[c * R * N + i];
+            qd[2 * c] = zz.x;
+            qd[2 * c + 1] = zz.y;
+        }
+        qd[8] = z[4 * R * N + i].x;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const TO q = (TO)qd[c];
+            out[c * cs + v] = q;
+            if (MODE == FS_P5_DOT) {
+                acc0 += (T)(pin[c * cs + v] * q);
+            } else if (MODE == FS_P5_RHS) {
+                acc0 += (T)(q * q);
+                acc1 += (double)(qd[c] * qd[c]);
+            }
+        }
+    }
+    if (MODE == FS_P5_PLAIN) return;
+    const int nb = gridDim.x;
+    double part[2];
+    part[0] = block_sum((double)acc0);
+    part[1] = (MODE == FS_P5_RHS) ? block_sum(acc1) : 0.0;
+    if (!publish_partials<2>(part, a.partials, blockIdx.x, nb, &cg->ticket)) return;
+    double tot[2];
+    reduce_partials<2>(a.partials, nb, &cg->ticket, tot);
+    if (tid != 0) return;
+    if (MODE == FS_P5_DOT)
+        cg_after_dot(cg, tot[0]);
+    else
+        cg_start(cg, tot[0], tot[1]);
+}
+
+// ------------------------------------------------------------------ launcher
+enum FsPassKind : int {
+    FK_P1_PLAIN_F64, FK_P1_PLAIN_F32, FK_P1_TAN_F64, FK_P1_TAN_F32, FK_P1_CG_F64, FK_P1_CG_F32,
+    FK_P2_F64, FK_P2_F32, FK_P3_F64, FK_P3_F32, FK_P4_F64, FK_P4_F32,
+    FK_P5_PLAIN_F64, FK_P5_PLAIN_F32, FK_P5_DOT_F64, FK_P5_DOT_F32,
+    FK_P5_RHS_F64_TO_F64, FK_P5_RHS_F64_TO_F32,
+    FK_COUNT
+};
+
+int fs_row_blocks(int N, bool fp64);
+
+cudaError_t run_fs_pass(int N, FsPassKind kind, const FsArgs& a, cudaStream_t s);
+
+template <int N>
+cudaError_t run_fs_pass_n(FsPassKind kind, const FsArgs& a, cudaStream_t s);
+
+template <typename K>
+static cudaError_t launch_fs(K kernel, dim3 grid, int threads, size_t smem, const FsArgs& a, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The x2 passes are the small-strain kernels over nine components; they
+// read the spectrum, the twiddles and (when set) the CG state.
+template <int N, typename T, bool FWD>
+static cudaError_t launch_fs_p24(const FsArgs& a, cudaStream_t s) {
+    using C = Cfg<N, T>;
+    PassArgs b{};
+    b.out = a.out;
+    b.cg = a.cg;
+    b.tw = a.tw;
+    const dim3 g((C::H + C::W2 - 1) / C::W2, (kFsComp * N + C::S2 - 1) / C::S2, 1);
+    cudaError_t e = cudaFuncSetAttribute(k_p24<N, T, FWD, kFsComp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::smem_p24);
+    if (e != cudaSuccess) return e;
+    k_p24<N, T, FWD, kFsComp><<<g, C::T2, C::smem_p24, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t run_fs_pass_n(FsPassKind kind, const FsArgs& a, cudaStream_t s) {
+    using C32 = FsCfg<N, float>;
+    using C64 = FsCfg<N, double>;
+    const dim3 r32(C32::row_blocks), r64(C64::row_blocks);
+    const dim3 g32((C32::H + C32::W3 - 1) / C32::W3, N), g64((C64::H + C64::W3 - 1) / C64::W3, N);
+    const size_t m32 = C32::smem_rows, m64 = C64::smem_rows;
+    switch (kind) {
+        case FK_P1_PLAIN_F64: return launch_fs(k_fs_p1<N, double, FS_P1_PLAIN>, r64, kThreads, m64, a, s);
+        case FK_P1_PLAIN_F32: return launch_fs(k_fs_p1<N, float, FS_P1_PLAIN>, r32, kThreads, m32, a, s);
+        case FK_P1_TAN_F64: return launch_fs(k_fs_p1<N, double, FS_P1_TAN>, r64, kThreads, m64, a, s);
+        case FK_P1_TAN_F32: return launch_fs(k_fs_p1<N, float, FS_P1_TAN>, r32, kThreads, m32, a, s);
+        case FK_P1_CG_F64: return launch_fs(k_fs_p1<N, double, FS_P1_CG>, r64, kThreads, m64, a, s);
+        case FK_P1_CG_F32: return launch_fs(k_fs_p1<N, float, FS_P1_CG>, r32, kThreads, m32, a, s);
+        case FK_P2_F64: return launch_fs_p24<N, double, true>(a, s);
+        case FK_P2_F32: return launch_fs_p24<N, float, true>(a, s);
+        case FK_P4_F64: return launch_fs_p24<N, double, false>(a, s);
+        case FK_P4_F32: return launch_fs_p24<N, float, false>(a, s);
+        case FK_P3_F64: return launch_fs(k_fs_p3<N, double>, g64, C64::T3, C64::smem_p3, a, s);
+        case FK_P3_F32: return launch_fs(k_fs_p3<N, float>, g32, C32::T3, C32::smem_p3, a, s);
+        case FK_P5_PLAIN_F64: return launch_fs(k_fs_p5<N, double, FS_P5_PLAIN, double>, r64, kThreads, m64, a, s);
+        case FK_P5_PLAIN_F32: return launch_fs(k_fs_p5<N, float, FS_P5_PLAIN, float>, r32, kThreads, m32, a, s);
+        case FK_P5_DOT_F64: return launch_fs(k_fs_p5<N, double, FS_P5_DOT, double>, r64, kThreads, m64, a, s);
+        case FK_P5_DOT_F32: return launch_fs(k_fs_p5<N, float, FS_P5_DOT, float>, r32, kThreads, m32, a, s);
+        case FK_P5_RHS_F64_TO_F64:
+            return launch_fs(k_fs_p5<N, double, FS_P5_RHS, double>, r64, kThreads, m64, a, s);
+        case FK_P5_RHS_F64_TO_F32:
+            return launch_fs(k_fs_p5<N, double, FS_P5_RHS, float>, r64, kThreads, m64, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fftg

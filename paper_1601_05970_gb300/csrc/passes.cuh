@@ -341,8 +341,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 2) k
 
 // -------------------------------------------------------------- P2 / P4 (x2)
 // Blocks of T2 = (slabs x columns x N2) threads: stage A is one item per
-// thread; stage B takes N1/N2 rounds.
-template <int N, typename T, bool FWD>
+// thread; stage B takes N1/N2 rounds. A slab is one (component, x1) plane
+// of the spectrum; NC components (6 here, 9 in the finite-strain passes).
+template <int N, typename T, bool FWD, int NC = 6>
 __global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int H = C::H, W = C::W2, S = C::S2, NT = C::T2;
@@ -363,28 +364,28 @@ __global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
         for (int it = tid; it < P * N2; it += NT) {
             const int pc = it % P, t = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
-            if (col < H && slab < 6 * N)
+            if (col < H && slab < NC * N)
                 fwdA<N, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, t, tw);
         }
         __syncthreads();
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
-            if (col < H && slab < 6 * N)
+            if (col < H && slab < NC * N)
                 fwdB<N, true, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, k1, tw);
         }
     } else {
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
-            if (col < H && slab < 6 * N)
+            if (col < H && slab < NC * N)
                 invB<N, true, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, k1, tw);
         }
         __syncthreads();
         for (int it = tid; it < P * N2; it += NT) {
             const int pc = it % P, t = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
-            if (col < H && slab < 6 * N)
+            if (col < H && slab < NC * N)
                 invA<N, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, t, tw);
         }
     }
@@ -644,41 +645,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 2) k
     double tot[2];
     reduce_partials<2>(partials, nb, &cg->ticket, tot);
     if (tid != 0) return;
-    if (MODE == P5_DOT) {
-        const double pq = tot[0];
-        cg->pq = pq;
-        cg->pend = 0;  // P1 of this iteration has added the previous step
-        if (!isfinite(pq)) {
-            cg->done = CG_BREAKDOWN;
-        } else if (cg->omega > 0.0) {
-            cg->alpha = cg->omega;  // Richardson: fixed step, <p, q> unused
-        } else if (!(pq > 0.0)) {
-            cg->done = cg->stag_window > 0 ? CG_STAGNATED : CG_BREAKDOWN;
-        } else {
-            cg->alpha = cg->rr / pq;
-        }
-    } else {
-        const double rr = tot[0], gs2 = tot[1];
-        cg->rr = rr;
-        cg->rr0 = rr;
-        cg->rr_min = rr;
-        cg->it_min = 0;
-        cg->gs2 = gs2;
-        cg->it = 0;
-        cg->beta = 0.0;
-        cg->alpha = 0.0;
-        const double stop2 = fmax(cg->tol2 * rr, cg->floor2);
-        cg->stop2 = stop2;
-        if (!isfinite(rr) || !isfinite(gs2)) {
-            cg->done = CG_BREAKDOWN;
-        } else if (gs2 <= cg->floor2 || rr == 0.0) {
-            cg->done = CG_CONVERGED;
-        } else if (cg->fixed_it <= 0 && rr <= stop2) {
-            cg->done = CG_CONVERGED;
-        } else {
-            cg->done = CG_RUNNING;
-        }
-    }
+    if (MODE == P5_DOT)
+        cg_after_dot(cg, tot[0]);
+    else
+        cg_start(cg, tot[0], tot[1]);
 }
 
 // ------------------------------------------------------------------ launcher

@@ -325,28 +325,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(VecArgs a) {
     double tot[1];
     reduce_partials<1>(partials, gridDim.x, &cg->ticket, tot);
     if (threadIdx.x != 0) return;
-    const double rr = tot[0];
-    const int it = cg->it + 1;
-    cg->it = it;
-    cg->pend = 1;
-    cg->beta = cg->omega > 0.0 ? 0.0 : rr / cg->rr;  // Richardson: p = r
-    cg->rr = rr;
-    if (!isfinite(rr)) {
-        cg->done = CG_BREAKDOWN;
-    } else if (cg->fixed_it > 0) {
-        if (it >= cg->fixed_it) cg->done = CG_CONVERGED;
-    } else if (rr <= cg->stop2) {
-        cg->done = CG_CONVERGED;
-    } else if (it >= cg->max_it) {
-        cg->done = CG_MAXIT;
-    } else if (cg->stag_window > 0) {
-        if (rr < cg->rr_min) {
-            cg->rr_min = rr;
-            cg->it_min = it;
-        } else if (it - cg->it_min >= cg->stag_window) {
-            cg->done = CG_STAGNATED;
-        }
-    }
+    cg_after_update(cg, tot[0]);
 }
 
 // After the last CG iteration: x += alpha p where the last update left the

@@ -1,8 +1,9 @@
-"""Thin Python binding of the fftg C-ABI (include/fftg.h).
+"""Thin Python binding of the fftg C-ABI (include/fftg.h, include/fftg_fs.h).
 
 Argument marshalling only: every step of the solver runs in the CUDA
 kernels of libfftg.so. The functions keep the C names; `Cell` wraps a
-handle with PyTorch-allocated device memory and the current torch stream.
+small-strain handle with PyTorch-allocated device memory and the current
+torch stream, `FsCell` a finite-strain handle.
 There is no CPU fallback: if the library is missing, loading it raises.
 """
 from __future__ import annotations
@@ -33,6 +34,8 @@ FFTG_FIELD_STRESS = 1
 FFTG_FIELD_EPBAR = 2
 FFTG_FIELD_EPS_P = 3
 FFTG_MAX_NEWTON_LOG = 64
+FFTG_FS_FIELD_DEFGRAD = 0
+FFTG_FS_FIELD_STRESS = 1
 
 ERRORS = {
     FFTG_EINVAL: "invalid argument",
@@ -54,6 +57,19 @@ class FftgError(RuntimeError):
 class fftg_phase(C.Structure):
     _fields_ = [("K", C.c_double), ("G", C.c_double), ("sigma_y", C.c_double), ("H", C.c_double),
                 ("n", C.c_double), ("eps0", C.c_double), ("t0", C.c_double), ("model", C.c_int)]
+
+
+class fftg_svk_phase(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("mu", C.c_double)]
+
+
+def svk_array(mats):
+    """fftg_svk_phase[] from (lambda, mu) pairs or objects with as_tuple()."""
+    arr = (fftg_svk_phase * len(mats))()
+    for i, m in enumerate(mats):
+        lam, mu = m.as_tuple() if hasattr(m, "as_tuple") else m
+        arr[i].lambda_, arr[i].mu = float(lam), float(mu)
+    return arr
 
 
 def phase_array(mats):
@@ -140,6 +156,21 @@ SIGNATURES = {
                                             C.c_void_p, C.c_int, C.POINTER(fftg_phase), C.c_int,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _D6,
                                             C.c_void_p]),
+    "fftg_fs_workspace_size": (C.c_int, [C.c_int, C.POINTER(fftg_options), C.POINTER(C.c_size_t)]),
+    "fftg_fs_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint8), C.c_int,
+                                 C.POINTER(fftg_svk_phase), C.POINTER(fftg_options)]),
+    "fftg_fs_step": (C.c_int, [C.c_void_p, _D6, C.c_double, C.c_double, _D6,
+                               C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fftg_fs_last_stats": (C.c_int, [C.c_void_p, C.POINTER(fftg_stats)]),
+    "fftg_fs_get_field": (C.c_int, [C.c_void_p, C.c_int, _D6]),
+    "fftg_fs_op_project": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "fftg_fs_op_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, _D6]),
+    "fftg_fs_profile_kinds": (C.c_int, []),
+    "fftg_fs_profile_name": (C.c_char_p, [C.c_int]),
+    "fftg_fs_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "fftg_fs_profile_read": (C.c_int, [C.c_void_p, C.c_int, _D6, C.POINTER(C.c_longlong)]),
+    "fftg_fs_launch_count": (C.c_longlong, [C.c_void_p]),
+    "fftg_fs_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -429,3 +460,115 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+class FsCell:
+    """A finite-strain handle (include/fftg_fs.h): one periodic cell of
+    St. Venant-Kirchhoff phases loaded by a macroscopic deformation gradient.
+
+    phase: uint8 [N, N, N]; mats: (lambda, mu) pairs or objects with
+    as_tuple(). Tensors are 3x3 (row major in the C calls)."""
+
+    def __init__(self, N, phase, mats, precision="mixed", max_newton=50, max_cg=2000,
+                 cg_inner_floor=1e-5, fixed_cg=0, fixed_newton=0, device=None, stream=None,
+                 cg_graph=1):
+        import torch
+
+        lib = load()
+        self.N = int(N)
+        self.V = self.N ** 3
+        opt = default_options()
+        opt.precision = FFTG_MIXED if precision == "mixed" else FFTG_FP64
+        opt.max_newton = max_newton
+        opt.max_cg = max_cg
+        opt.cg_inner_floor = cg_inner_floor
+        opt.fixed_cg = fixed_cg
+        opt.fixed_newton = fixed_newton
+        opt.cg_graph = cg_graph
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        self.precision = precision
+        ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8).reshape(-1))
+        m = svk_array(mats)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib.fftg_fs_create(C.byref(h), self.N, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                     len(mats), m, C.byref(opt)), "fftg_fs_create")
+        self.h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.fftg_fs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, dF, tol_newton, tol_cg):
+        """One increment: Fbar += dF (3x3); returns (mean P 3x3, Newton
+        iterations, CG iterations)."""
+        dF = np.ascontiguousarray(dF, dtype=np.float64).reshape(9)
+        P = np.zeros(9)
+        nn, nc = C.c_int(0), C.c_int(0)
+        check(self._lib.fftg_fs_step(self.h, _dptr(dF), tol_newton, tol_cg, _dptr(P),
+                                     C.byref(nn), C.byref(nc)), "fftg_fs_step")
+        return P.reshape(3, 3), nn.value, nc.value
+
+    def stats(self):
+        s = fftg_stats()
+        check(self._lib.fftg_fs_last_stats(self.h, C.byref(s)), "fftg_fs_last_stats")
+        n = min(s.newton_iters, FFTG_MAX_NEWTON_LOG)
+        return dict(status=s.status, newton_iters=s.newton_iters, cg_iters=s.cg_iters,
+                    cg_per_newton=list(s.cg_per_newton[:n]),
+                    newton_norm=list(s.newton_norm[:n]), residual=list(s.residual[:n]),
+                    cg_relres=list(s.cg_relres[:n]), cg_status=list(s.cg_status[:n]))
+
+    def field(self, which):
+        out = np.zeros(9 * self.V)
+        check(self._lib.fftg_fs_get_field(self.h, which, _dptr(out)), "fftg_fs_get_field")
+        return out.reshape((3, 3) + (self.N,) * 3)
+
+    def project(self, A, out=None):
+        """G A for a device tensor A with 9 * N^3 elements (float64 or float32)."""
+        import torch
+        assert A.is_cuda and A.is_contiguous() and A.numel() == 9 * self.V
+        prec = FFTG_FP64 if A.dtype == torch.float64 else FFTG_MIXED
+        if out is None:
+            out = torch.empty_like(A)
+        check(self._lib.fftg_fs_op_project(self.h, prec, C.c_void_p(A.data_ptr()),
+                                           C.c_void_p(out.data_ptr())), "fftg_fs_op_project")
+        return out
+
+    def matvec(self, p, q=None):
+        """q = G (K : p) at the committed state; returns (q, <p, q>)."""
+        import torch
+        assert p.is_cuda and p.is_contiguous() and p.numel() == 9 * self.V
+        prec = FFTG_FP64 if p.dtype == torch.float64 else FFTG_MIXED
+        if q is None:
+            q = torch.empty_like(p)
+        pq = C.c_double(0.0)
+        check(self._lib.fftg_fs_op_matvec(self.h, prec, C.c_void_p(p.data_ptr()),
+                                          C.c_void_p(q.data_ptr()), C.byref(pq)), "fftg_fs_op_matvec")
+        return q, pq.value
+
+    def profile(self, on=True):
+        check(self._lib.fftg_fs_profile_enable(self.h, int(bool(on))), "fftg_fs_profile_enable")
+
+    def profile_read(self):
+        """{kernel kind name: (total device ms, launches)} since profiling was enabled."""
+        out = {}
+        for k in range(self._lib.fftg_fs_profile_kinds()):
+            ms, n = C.c_double(0.0), C.c_longlong(0)
+            check(self._lib.fftg_fs_profile_read(self.h, k, C.byref(ms), C.byref(n)),
+                  "fftg_fs_profile_read")
+            if n.value:
+                out[self._lib.fftg_fs_profile_name(k).decode()] = (ms.value, n.value)
+        return out
+
+    def launches(self):
+        return int(self._lib.fftg_fs_launch_count(self.h))

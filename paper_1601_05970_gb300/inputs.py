@@ -224,6 +224,14 @@ def uniaxial_path(e11_max: float, n_inc: int) -> np.ndarray:
     return dE
 
 
+def stretch_shear_path(n_inc: int) -> np.ndarray:
+    """Finite-strain load path: n_inc equal increments dF of the macroscopic
+    deformation gradient, [n_inc, 3, 3]; each stretches x1 by 1 %, shears
+    (F12) by 0.5 % and contracts x2 and x3 by 0.4 %."""
+    dF = np.array([[0.01, 0.005, 0.0], [0.0, -0.004, 0.0], [0.0, 0.0, -0.004]])
+    return np.repeat(dF[None], n_inc, axis=0)
+
+
 def frobenius6(v) -> float:
     """Frobenius norm of a symmetric tensor given as 6 components."""
     v = np.asarray(v, dtype=np.float64)
@@ -271,4 +279,13 @@ def workload(name: str, seed: int | None = None):
                     tol_newton=1e-5, tol_cg=1e-8, fraction=frac, seed=seed,
                     desc=f"243^3 random spheres r in [3,8], hard fraction 0.2, "
                          f"seed {seed}, uniaxial strain E11 to 0.03 in 20 increments")
+    if name == "fs_spheres243":
+        N = 243
+        seed = 2 if seed is None else seed
+        ph, frac, _ = random_spheres(N, 0.2, seed=seed)
+        return dict(N=N, phase=ph, mats=SVK_TWO_PHASE, dF=stretch_shear_path(20),
+                    tol_newton=1e-6, tol_cg=1e-8, fraction=frac, seed=seed,
+                    desc=f"243^3 random spheres r in [3,8], hard fraction 0.2, seed {seed}, "
+                         f"St. Venant-Kirchhoff phases (hard 5x soft), F11 to 1.2 with "
+                         f"F12 to 0.1 and lateral contraction in 20 increments")
     raise KeyError(name)

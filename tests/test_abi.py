@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every symbol include/fftg.h declares.
+"""The C-ABI library loads and exports every symbol include/*.h declares.
 
 No compute calls: this runs without a GPU.
 """
@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "fftg.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(fftg_[a-z_0-9]+)\s*\(", src)))
 
@@ -67,12 +68,14 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"fftg_phase": fftg.fftg_phase, "fftg_options": fftg.fftg_options,
-               "fftg_stats": fftg.fftg_stats, "fftg_result": fftg.fftg_result}
-    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fftg.h"', "int main(void) {"]
+               "fftg_stats": fftg.fftg_stats, "fftg_result": fftg.fftg_result,
+               "fftg_svk_phase": fftg.fftg_svk_phase}
+    cname = {"lambda_": "lambda"}   # a Python keyword in the ctypes mirror
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fftg_fs.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
         for f in cls._fields_:
-            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {cname.get(f[0], f[0])}));')
     lines += ["return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -120,3 +123,34 @@ def test_create_rejects_invalid_phases(lib):
     h = C.c_void_p()
     assert lib.fftg_create(C.byref(h), 3, ph.ctypes.data_as(C.POINTER(C.c_uint8)), 1,
                            fftg.phase_array((I.SOFT,)), C.byref(o)) == fftg.FFTG_EINVAL
+
+
+def test_finite_strain_create_rejects_bad_arguments(lib):
+    # host-side checks, before any device work
+    import ctypes as C
+    ph = np.zeros(27, np.uint8)
+    php = ph.ctypes.data_as(C.POINTER(C.c_uint8))
+    good = fftg.svk_array(((0.5, 0.4),))
+    h = C.c_void_p()
+    for m in (((-0.1, 0.4),), ((0.5, 0.0),), ((float("nan"), 0.4),)):
+        assert lib.fftg_fs_create(C.byref(h), 3, php, 1, fftg.svk_array(m), None) == fftg.FFTG_EINVAL
+    for bad_n in (2, 7, 729):
+        assert lib.fftg_fs_create(C.byref(h), bad_n, php, 1, good, None) == fftg.FFTG_EINVAL
+    ph2 = ph.copy()
+    ph2[5] = 1                                                   # phase id >= nphase
+    assert lib.fftg_fs_create(C.byref(h), 3, ph2.ctypes.data_as(C.POINTER(C.c_uint8)), 1, good,
+                              None) == fftg.FFTG_EINVAL
+    o = fftg.default_options()
+    o.solver = fftg.FFTG_SOLVER_RICHARDSON                       # CG only
+    assert lib.fftg_fs_create(C.byref(h), 3, php, 1, good, C.byref(o)) == fftg.FFTG_EINVAL
+    o = fftg.default_options()
+    o.workspace = C.c_void_p(256)                                # own memory only
+    assert lib.fftg_fs_create(C.byref(h), 3, php, 1, good, C.byref(o)) == fftg.FFTG_EINVAL
+    b = C.c_size_t()
+    o = fftg.default_options()
+    assert lib.fftg_fs_workspace_size(45, C.byref(o), C.byref(b)) == 0
+    mixed = b.value
+    o.precision = fftg.FFTG_FP64
+    assert lib.fftg_fs_workspace_size(45, C.byref(o), C.byref(b)) == 0
+    assert b.value > mixed > 0
+    assert lib.fftg_fs_profile_kinds() > 0 and lib.fftg_fs_profile_name(0).startswith(b"fs_")
