@@ -61,19 +61,32 @@ def bytes_per_voxel(N):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the dominant kernel from one ncu capture (profiles/traffic_cg_kernels_
-# spheres243.md), valid while the kernel sources have the digest they had
-# then (SHA-256 prefix of csrc/common.cuh + fft_core.cuh + passes.cuh).
-TRAFFIC = {"p1_cg_f32": {"N": 243, "bytes": 2417.8e6, "digest": "a092d4a63a450e6d"}}
+# the dominant kernels from one ncu capture each (profiles/traffic_cg_kernels_
+# spheres243.md, profiles/traffic_fs_cg_kernels_spheres243.md), valid while
+# the kernel sources have the digest they had then (SHA-256 prefix of the
+# files listed).
+KERNEL_FILES = ("common.cuh", "fft_core.cuh", "passes.cuh")
+FS_KERNEL_FILES = KERNEL_FILES + ("fs_passes.cuh",)
+TRAFFIC = {"p1_cg_f32": {"N": 243, "bytes": 2417.9e6, "digest": "f6e1e0bd0ee970a9", "files": KERNEL_FILES},
+           "fs_p1_cg_f32": {"N": 243, "bytes": 3579.5e6, "digest": "ea36263b5f2aa9da", "files": FS_KERNEL_FILES}}
 
 
-def kernel_digest():
+def kernel_digest(files=KERNEL_FILES):
     import hashlib
     h = hashlib.sha256()
-    for f in ("common.cuh", "fft_core.cuh", "passes.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1601_05970_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def measured_traffic(kind, N):
+    """The captured DRAM bytes per launch of `kind` at N^3, or None when the
+    kernel sources have changed since the capture."""
+    tr = TRAFFIC.get(kind)
+    if tr and tr["N"] == N and tr["digest"] == kernel_digest(tr["files"]):
+        return tr["bytes"]
+    return None
 
 
 def parse():
@@ -91,6 +104,8 @@ def parse():
                     help="skip the FP64 comparison, the batched and the serving runs")
     ap.add_argument("--no-graph", action="store_true",
                     help="enqueue CG iterations from the host instead of the graph loop")
+    ap.add_argument("--finite-strain-only", action="store_true",
+                    help="run only the finite-strain line (mixed, --N 243 or 135) and print it")
     ap.add_argument("--serve-rate", type=float, default=100.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     return ap.parse_args()
@@ -295,15 +310,16 @@ def fs_bytes_per_voxel(N):
             "fs_p5_dot_f32": s32 + 36 + 36, "fs_cg_update_f32": 3 * 36}
 
 
-def finite_strain_line(warm=1, timed=2):
+def finite_strain_line(N=243, warm=1, timed=2):
     """The finite-strain extension (St. Venant-Kirchhoff, first
-    Piola-Kirchhoff stress, gradient projection) on the 243^3 spheres cell,
-    mixed precision: increments warm.. of the stretch-shear path timed with
-    CUDA events and per-kernel events, the roofline of its dominant kernel."""
+    Piola-Kirchhoff stress, gradient projection) on the N^3 spheres cell
+    (243 or 135), mixed precision: increments warm.. of the stretch-shear
+    path timed with CUDA events and per-kernel events, the roofline of its
+    dominant kernel."""
     import torch
     from paper_1601_05970_gb300 import fftg
     from paper_1601_05970_gb300 import inputs as I
-    w = I.workload("fs_spheres243")
+    w = I.workload(f"fs_spheres{N}")
     N = w["N"]
     V = N ** 3
     cell = fftg.FsCell(N, w["phase"], w["mats"], precision="mixed")
@@ -339,13 +355,13 @@ def finite_strain_line(warm=1, timed=2):
     alg = eff[kind] * V * bpv[kind]
     achieved = alg / (kms * 1e-3) / 1e9
     return {
-        "metric": "CG-iter voxels/s at 243^3, finite strain (FP32-inner mixed precision)",
+        "metric": f"CG-iter voxels/s at {N}^3, finite strain (FP32-inner mixed precision)",
         "value": V * nc_tot / (dev_ms * 1e-3), "unit": UNIT,
-        "e2e_value": V * nc_tot / wall, "workload": "fs_spheres243-stretch-shear",
+        "e2e_value": V * nc_tot / wall, "workload": f"fs_spheres{N}-stretch-shear",
         "increments_timed": timed, "newton_iters": nn_tot, "cg_iters": nc_tot,
         "P": [float(v) for v in P.reshape(-1)], "ms": dev_ms, "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": kind,
+                     "frac": achieved / hbm, "traffic": measured_traffic(kind, N), "kernel": kind,
                      "peak_source": peak_kind, "bytes_per_launch": alg / max(eff[kind], 1),
                      "avg_launch_ms": kms / max(eff[kind], 1)},
         "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in sorted(
@@ -426,6 +442,10 @@ def main():
     from paper_1601_05970_gb300 import inputs as I
     build.build()
     fftg.load()
+    if args.finite_strain_only:
+        if rank == 0:
+            print(json.dumps(finite_strain_line(args.N)))
+        return 0
 
     N = args.N
     w = I.workload("spheres243" if N == 243 else "spheres135", seed=rank_seed(rank))
@@ -504,8 +524,7 @@ def main():
         alg_bytes = eff[kind] * V * bpv[kind]
         achieved = alg_bytes / (kms * 1e-3) / 1e9
         per_launch = alg_bytes / max(eff[kind], 1)
-        tr = TRAFFIC.get(kind)
-        traffic = tr["bytes"] if tr and tr["N"] == N and tr["digest"] == kernel_digest() else None
+        traffic = measured_traffic(kind, N)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "kernel": kind,
                 "peak_source": peak_kind, "bytes_per_launch": per_launch,

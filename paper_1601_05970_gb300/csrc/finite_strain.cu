@@ -62,6 +62,13 @@ inline int fs_point_blocks(long long V) {
     return (int)(b < kFsPointBlocks ? b : kFsPointBlocks);
 }
 
+// Grid of the vectorised CG update: one thread per 16-byte vector of a
+// component, capped (depends only on the grid size).
+inline int fs_vector_blocks(long long cs, int elem_bytes) {
+    const long long b = (cs / (16 / elem_bytes) + kThreads - 1) / kThreads;
+    return (int)(b < kFsPointBlocks ? b : kFsPointBlocks);
+}
+
 // Scalars of one constitutive evaluation / Newton update.
 struct FsDev {
     double p2;       // ||P||^2 (Frobenius, summed over voxels)
@@ -158,23 +165,38 @@ __global__ void __launch_bounds__(kThreads) k_fs_constitutive(FsPointArgs a) {
 }
 
 // r -= alpha q; <r, r>; beta and the stopping tests (x += alpha p deferred
-// to the next P1 or to k_fs_cg_finish).
+// to the next P1 or to k_fs_cg_finish). 16-byte vectors over the padded
+// components, all loads of an item before its stores; lanes in the padding
+// are updated too (harmless) but left out of <r, r>.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fs_cg_update(FsPointArgs a) {
     CGState* cg = a.cg;
     if (cg->done) return;
-    const long long V = a.V, cs = a.cs;
+    constexpr int VW = 16 / (int)sizeof(T);
+    using VT = typename Vec16<T>::type;
+    const long long V = a.V, nv = a.cs / VW;
     const T alpha = (T)cg->alpha;
-    T* r = (T*)a.r;
-    const T* q = (const T*)a.q;
+    VT* r = (VT*)a.r;
+    const VT* q = (const VT*)a.q;
     T acc = T(0);
-    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
-         v += (long long)gridDim.x * kThreads) {
+    for (long long j = (long long)blockIdx.x * kThreads + threadIdx.x; j < nv;
+         j += (long long)gridDim.x * kThreads) {
+        VT rv[9], qv[9];
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            const T rv = r[c * cs + v] - alpha * q[c * cs + v];
-            r[c * cs + v] = rv;
-            acc += rv * rv;
+            rv[c] = r[c * nv + j];
+            qv[c] = q[c * nv + j];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            T* re = reinterpret_cast<T*>(&rv[c]);
+            const T* qe = reinterpret_cast<const T*>(&qv[c]);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                re[e] -= alpha * qe[e];
+                if (j * VW + e < V) acc += re[e] * re[e];
+            }
+            r[c * nv + j] = rv[c];
         }
     }
     double part[1] = {block_sum((double)acc)};
@@ -493,9 +515,9 @@ int fs_cg_iteration(fftg_fs_handle* h) {
     FsPointArgs u = point_args(h);
     const int slot = fs_prof_begin(h, f64 ? FSK_CG_UPDATE_F64 : FSK_CG_UPDATE_F32);
     if (f64)
-        k_fs_cg_update<double><<<fs_point_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        k_fs_cg_update<double><<<fs_vector_blocks(h->cs, 8), kThreads, 0, h->stream>>>(u);
     else
-        k_fs_cg_update<float><<<fs_point_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        k_fs_cg_update<float><<<fs_vector_blocks(h->cs, 4), kThreads, 0, h->stream>>>(u);
     fs_prof_end(h, slot);
     CK(cudaGetLastError());
     return FFTG_OK;
@@ -735,14 +757,12 @@ int fftg_fs_create(fftg_fs_handle** out, int N, const uint8_t* phase, int nphase
     const double I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     std::memcpy(h->h_Fbar, I9, sizeof(I9));
     cudaStream_t s = h->stream;
-    if (cudaMemcpyAsync(h->phase, phase, V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (cudaMemsetAsync(h->ws, 0, L.total, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->phase, phase, V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->lame, lame.data(), lame.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw64, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw32, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->Fbar_dev, h->h_Fbar, 9 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(h->Fstar, 0, 9 * h->cs * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(h->cg, 0, sizeof(CGState), s) != cudaSuccess ||
-        cudaMemsetAsync(h->dev, 0, sizeof(FsDev), s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         h->last_cuda = cudaGetLastError();
         fftg_fs_destroy(h);

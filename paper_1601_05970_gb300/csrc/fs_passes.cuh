@@ -45,6 +45,33 @@ struct FsArgs {
     long long cs;          // component stride of the real fields (elements)
 };
 
+// Tuning: voxels per lane in the elementwise phases of P1 and P5 (moved as
+// one vector per component; FP64 at most 2), shared-memory budgets (KB) of
+// the row passes and of P3, and the minimum resident blocks per SM of the
+// FP32 P1 and P5 (a bound on their registers; the FP64 ones take what they
+// need: they are bound by FP64 arithmetic, not by memory). Set by timing
+// variants on the 243^3 finite-strain workload (per CG iteration, FP32):
+// one voxel per lane and 40 KB of rows (R = 4) gave P1 0.66 ms (3 or 4
+// blocks per SM alike; 4 spills a little) and P5 0.34 ms with 4 blocks per
+// SM (0.39 ms with 3); two voxels per lane 0.73-0.91 ms for P1 (it spills
+// at 3 blocks per SM); 80 KB of rows 0.76 ms; P3 with 100 or 64 KB of
+// columns 0.44 and 0.71 ms against 0.39 ms with 150 KB.
+#ifndef FFTG_FS_VW
+#define FFTG_FS_VW 1
+#endif
+#ifndef FFTG_FS_ROW_KB
+#define FFTG_FS_ROW_KB 40
+#endif
+#ifndef FFTG_FS_P3_KB
+#define FFTG_FS_P3_KB 150
+#endif
+#ifndef FFTG_FS_P1_MINB
+#define FFTG_FS_P1_MINB 3
+#endif
+#ifndef FFTG_FS_P5_MINB
+#define FFTG_FS_P5_MINB 4
+#endif
+
 template <int N, typename T>
 struct FsCfg {
     static constexpr int H = (N + 1) / 2;
@@ -54,16 +81,20 @@ struct FsCfg {
     }
     static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
     static constexpr int cap(int x) { return x > 1024 ? 1024 : x; }
-    // rows per block of P1/P5: five complex pencils per row in ~80 KB
-    static constexpr int R = fl2(80 * 1024 / (kFsPairs * N * CS));
-    // columns per block of P3: nine pencils per column in ~150 KB
-    static constexpr int W3 = fl2(150 * 1024 / (kFsComp * N * CS));
+    // rows per block of P1/P5: five complex pencils per row; a power of two
+    // >= 4, so a block's rows start on a 16-byte boundary of every component
+    static constexpr int R0 = fl2(FFTG_FS_ROW_KB * 1024 / (kFsPairs * N * CS));
+    static constexpr int R = R0 < 4 ? 4 : R0;
+    static constexpr int VW = (sizeof(T) == 8 && FFTG_FS_VW > 2) ? 2 : FFTG_FS_VW;
+    // columns per block of P3: nine pencils per column
+    static constexpr int W3 = fl2(FFTG_FS_P3_KB * 1024 / (kFsComp * N * CS));
     static constexpr int T3 = Plan<N>::N2 == 1 ? 256 : cap(rup32(kFsComp * W3 * Plan<N>::N2));
     static constexpr size_t smem_rows = (size_t)(kFsPairs * R * N + N) * CS;
     static constexpr size_t smem_p3 = (size_t)(kFsComp * W3 * N + N) * CS;
     static constexpr int row_blocks = (N * N + R - 1) / R;
     static_assert(smem_rows <= 227 * 1024 && smem_p3 <= 227 * 1024, "shared memory per block");
     static_assert(T3 <= 1024 && T3 % 32 == 0, "threads per block");
+    static_assert((R * N) % VW == 0 && (VW == 1 || VW == 2 || VW == 4), "vector width");
 };
 
 // tau = K(F) : d for St. Venant-Kirchhoff, from h = F - I.
@@ -114,9 +145,9 @@ __device__ __forceinline__ void svk_tangent_apply(const T (&h)[9], T lam, T mu, 
 // [x += alpha p; p = r + beta p]; tau = K : p or tau = input; x3 R2C FFT of
 // R rows per block.
 template <int N, typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_fs_p1(FsArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1) k_fs_p1(FsArgs a) {
     using C = FsCfg<N, T>;
-    constexpr int R = C::R, H = C::H;
+    constexpr int R = C::R, H = C::H, VW = C::VW;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -136,48 +167,94 @@ __global__ void __launch_bounds__(kThreads) k_fs_p1(FsArgs a) {
         alpha = (T)a.cg->alpha;
         first = a.cg->it == 0;
     }
-    for (int i = tid; i < R * N; i += kThreads) {
-        T s[9];
-        if (i < nel) {
-            const long long v = base + i;
-            T p[9];
+    // Elementwise phase: VW consecutive voxels per lane, one vector per
+    // component. Every load of an item is issued before its first store
+    // (the fields could alias as far as the compiler knows, which would
+    // otherwise serialise one round trip per component). In the last block
+    // a vector that straddles the end of the grid touches only the padding
+    // of each component (cs >= N^3 + 4), and its lanes past the grid belong
+    // to rows the FFT stages skip.
+    for (int j = tid; j < (R * N) / VW; j += kThreads) {
+        const int i0 = j * VW;
+        T s[9][VW];
+        if (i0 < nel) {
+            const long long v0 = base + i0;
+            T p[9][VW], h[9][VW];
+            int ph[VW];
             if (MODE == FS_P1_CG) {
                 const T* r = (const T*)a.aux;
                 T* pp = (T*)a.aux2;
                 T* xx = (T*)a.aux3;
+                T po[9][VW], xo[9][VW];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    p[c] = r[c * cs + v];
-                    if (!first) {
-                        const T po = pp[c * cs + v];
-                        xx[c * cs + v] += alpha * po;
-                        p[c] += beta * po;
+                for (int c = 0; c < 9; ++c) ldv<VW, T>(r + c * cs + v0, p[c]);
+                if (!first) {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        ldv<VW, T>(pp + c * cs + v0, po[c]);
+                        ldv<VW, T>(xx + c * cs + v0, xo[c]);
                     }
-                    pp[c * cs + v] = p[c];
                 }
+                const T* hg = (const T*)a.hgrad;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) ldv<VW, T>(hg + c * cs + v0, h[c]);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) ph[e] = a.phase[v0 + e];
+                if (!first) {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) {
+                            xo[c][e] += alpha * po[c][e];
+                            p[c][e] += beta * po[c][e];
+                        }
+                        stv<VW, T>(xx + c * cs + v0, xo[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 9; ++c) stv<VW, T>(pp + c * cs + v0, p[c]);
             } else {
                 const T* in = (const T*)a.in;
 #pragma unroll
-                for (int c = 0; c < 9; ++c) p[c] = in[c * cs + v];
+                for (int c = 0; c < 9; ++c) ldv<VW, T>(in + c * cs + v0, p[c]);
+                if (MODE == FS_P1_TAN) {
+                    const T* hg = (const T*)a.hgrad;
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) ldv<VW, T>(hg + c * cs + v0, h[c]);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) ph[e] = a.phase[v0 + e];
+                }
             }
-            if (MODE == FS_P1_PLAIN) {
 #pragma unroll
-                for (int c = 0; c < 9; ++c) s[c] = p[c];
-            } else {
-                const T* hg = (const T*)a.hgrad;
-                T h[9];
+            for (int e = 0; e < VW; ++e) {
+                if (MODE == FS_P1_PLAIN) {
 #pragma unroll
-                for (int c = 0; c < 9; ++c) h[c] = hg[c * cs + v];
-                const double* m = a.lame + 2 * a.phase[v];
-                svk_tangent_apply<T>(h, (T)m[0], (T)m[1], p, s);
+                    for (int c = 0; c < 9; ++c) s[c][e] = p[c][e];
+                } else {
+                    T he[9], pe[9], se[9];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        he[c] = h[c][e];
+                        pe[c] = p[c][e];
+                    }
+                    const double* m = a.lame + 2 * ph[e];
+                    svk_tangent_apply<T>(he, (T)m[0], (T)m[1], pe, se);
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) s[c][e] = se[c];
+                }
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 9; ++c) s[c] = T(0);
+            for (int c = 0; c < 9; ++c)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) s[c][e] = T(0);
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) z[c * R * N + i] = mk(s[2 * c], s[2 * c + 1]);
-        z[4 * R * N + i] = mk(s[8], T(0));
+        for (int e = 0; e < VW; ++e) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) z[c * R * N + i0 + e] = mk(s[2 * c][e], s[2 * c + 1][e]);
+            z[4 * R * N + i0 + e] = mk(s[8][e], T(0));
+        }
     }
     __syncthreads();
     constexpr int NP = kFsPairs * R;
@@ -295,7 +372,7 @@ __global__ void __launch_bounds__(FsCfg<N, T>::T3) k_fs_p3(FsArgs a) {
 // for DOT, the partials of <p, q> (then alpha), for RHS those of <r, r> in
 // TO and of ||G P||^2 in T (then the start of the CG solve).
 template <int N, typename T, int MODE, typename TO>
-__global__ void __launch_bounds__(kThreads) k_fs_p5(FsArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1) k_fs_p5(FsArgs a) {
     using C = FsCfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -344,25 +421,47 @@ __global__ void __launch_bounds__(kThreads) k_fs_p5(FsArgs a) {
     const TO* pin = (const TO*)a.aux;
     T acc0 = T(0);
     double acc1 = 0.0;
-    for (int i = tid; i < nel; i += kThreads) {
-        const long long v = base + i;
-        T qd[9];
+    // VO voxels per lane (at most 16 bytes of TO): p is loaded before q is
+    // stored. Lanes past the grid in the last block write only component
+    // padding and are left out of the sums.
+    constexpr int VO = (C::VW * (int)sizeof(TO) > 16) ? 16 / (int)sizeof(TO) : C::VW;
+    for (int j = tid; j < (R * N) / VO; j += kThreads) {
+        const int i0 = j * VO;
+        if (i0 >= nel) continue;
+        const long long v0 = base + i0;
+        TO pv[9][VO];
+        if (MODE == FS_P5_DOT) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const cplx<T> zz = z[c * R * N + i];
-            qd[2 * c] = zz.x;
-            qd[2 * c + 1] = zz.y;
+            for (int c = 0; c < 9; ++c) ldv<VO, TO>(pin + c * cs + v0, pv[c]);
         }
-        qd[8] = z[4 * R * N + i].x;
+        T qd[9][VO];
+        TO q[9][VO];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-            const TO q = (TO)qd[c];
-            out[c * cs + v] = q;
-            if (MODE == FS_P5_DOT) {
-                acc0 += (T)(pin[c * cs + v] * q);
-            } else if (MODE == FS_P5_RHS) {
-                acc0 += (T)(q * q);
-                acc1 += (double)(qd[c] * qd[c]);
+        for (int e = 0; e < VO; ++e) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const cplx<T> zz = z[c * R * N + i0 + e];
+                qd[2 * c][e] = zz.x;
+                qd[2 * c + 1][e] = zz.y;
+            }
+            qd[8][e] = z[4 * R * N + i0 + e].x;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) q[c][e] = (TO)qd[c][e];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) stv<VO, TO>(out + c * cs + v0, q[c]);
+        if (MODE == FS_P5_PLAIN) continue;
+#pragma unroll
+        for (int e = 0; e < VO; ++e) {
+            if (i0 + e >= nel) continue;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                if (MODE == FS_P5_DOT) {
+                    acc0 += (T)(pv[c][e] * q[c][e]);
+                } else {
+                    acc0 += (T)(q[c][e] * q[c][e]);
+                    acc1 += (double)(qd[c][e] * qd[c][e]);
+                }
             }
         }
     }

@@ -279,13 +279,13 @@ def workload(name: str, seed: int | None = None):
                     tol_newton=1e-5, tol_cg=1e-8, fraction=frac, seed=seed,
                     desc=f"243^3 random spheres r in [3,8], hard fraction 0.2, "
                          f"seed {seed}, uniaxial strain E11 to 0.03 in 20 increments")
-    if name == "fs_spheres243":
-        N = 243
+    if name in ("fs_spheres135", "fs_spheres243"):
+        N = int(name[len("fs_spheres"):])
         seed = 2 if seed is None else seed
         ph, frac, _ = random_spheres(N, 0.2, seed=seed)
         return dict(N=N, phase=ph, mats=SVK_TWO_PHASE, dF=stretch_shear_path(20),
                     tol_newton=1e-6, tol_cg=1e-8, fraction=frac, seed=seed,
-                    desc=f"243^3 random spheres r in [3,8], hard fraction 0.2, seed {seed}, "
+                    desc=f"{N}^3 random spheres r in [3,8], hard fraction 0.2, seed {seed}, "
                          f"St. Venant-Kirchhoff phases (hard 5x soft), F11 to 1.2 with "
                          f"F12 to 0.1 and lateral contraction in 20 increments")
     raise KeyError(name)
