@@ -53,8 +53,14 @@ extern "C" {
 
 #define FFTG_FP64   0  /* every step in FP64 */
 #define FFTG_MIXED  1  /* FP32 inner CG (FFT, projection, tangent contraction);
-                          FP64 return mapping, residual G sigma, Newton test and
-                          homogenised stress: Newton acts as iterative refinement */
+                          FP64 return mapping, Newton test and homogenised
+                          stress, and a residual G sigma from FP64 data with
+                          double-float FFTs (FFTG_DD): Newton acts as
+                          iterative refinement */
+#define FFTG_DD     2  /* fftg_op_project only: FP64 buffers, FFTs in
+                          double-float arithmetic (pairs of FP32 numbers,
+                          about 48 significant bits), as in the residual of
+                          the FFTG_MIXED path */
 
 /* ---------------------------------------------------------------- fields */
 #define FFTG_FIELD_STRAIN  0  /* total strain E + eps*, [6][N^3] */
@@ -232,7 +238,9 @@ void fftg_destroy(fftg_handle* h);
 
 /* out = G tau (Eq. discrete_projection) for a real field tau [6][N^3]:
  * forward DFT, Ghat of Appendix A Eq. (FT_projection) at every frequency
- * (Ghat(0) = 0), inverse DFT. tau and out may alias. */
+ * (Ghat(0) = 0), inverse DFT. tau and out may alias. precision: FFTG_FP64
+ * (double buffers), FFTG_MIXED (float buffers) or FFTG_DD (double buffers,
+ * double-float FFTs). */
 int fftg_op_project(fftg_handle* h, int precision, const void* tau_dev, void* out_dev);
 
 /* Evaluate the constitutive law at E_trial + eps where E_trial = E + dE

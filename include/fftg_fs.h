@@ -23,6 +23,8 @@
  *  - A tensor field is [9][N][N][N] (component slowest, then x1, x2, x3).
  *  - Grids: N odd, a product of 3s and 5s, 3 <= N <= 243 (the grid sizes of
  *    fftg.h).
+ *  - Precision as in fftg.h: FFTG_MIXED runs the CG in FP32 and the
+ *    residual G P from FP64 stresses with double-float FFTs.
  *  - Return values are FFTG_OK or FFTG_E*; on error the committed state
  *    (Fbar, F*) is unchanged. The caller owns host arrays; the handle owns
  *    its device memory; one host thread uses a handle at a time.
@@ -50,7 +52,8 @@ typedef struct {
 
 /* Create a cell. phase: uint8 [N][N][N], values < nphase (<= 256); mats:
  * nphase phases. Options used: precision (FFTG_FP64, or FFTG_MIXED: FP32
- * inner CG with an FP64 residual, stress, Newton test and P, as in fftg.h),
+ * inner CG; FP64 stress, Newton test and mean P; the residual from the FP64
+ * stress with double-float FFTs, as in fftg.h),
  * max_newton, max_cg, cg_inner_floor, fixed_cg, fixed_newton, stream,
  * cg_graph. A workspace, solver != FFTG_SOLVER_CG or an invalid value of
  * the others gives FFTG_EINVAL; the rest are ignored. NULL opt: defaults.
@@ -74,9 +77,11 @@ int fftg_fs_last_stats(fftg_fs_handle* h, fftg_stats* out);
 /* Copy a committed field (FFTG_FS_FIELD_*) to host memory, FP64 [9][N^3]. */
 int fftg_fs_get_field(fftg_fs_handle* h, int which, double* host_out);
 
-/* out = G A for a device field A [9][N^3] (FP64 for FFTG_FP64, FP32 for
- * FFTG_MIXED): forward DFT, Ghat above at every frequency, inverse DFT.
- * A and out may alias. Enqueued on the handle's stream. */
+/* out = G A for a device field A [9][N^3] (FP64 for FFTG_FP64 and FFTG_DD,
+ * FP32 for FFTG_MIXED, which needs a mixed handle): forward DFT, Ghat above
+ * at every frequency, inverse DFT; FFTG_DD runs the FFTs in double-float
+ * arithmetic, as the mixed path's residual does. A and out may alias.
+ * Enqueued on the handle's stream. */
 int fftg_fs_op_project(fftg_fs_handle* h, int precision, const void* A_dev, void* out_dev);
 
 /* q = G (K : p) with K = dP/dF at the committed F (St. Venant-Kirchhoff's

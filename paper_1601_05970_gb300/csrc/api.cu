@@ -90,7 +90,8 @@ const char* const kKindNames[KK_COUNT] = {
     "p1_plain_f64", "p1_plain_f32", "p1_tan_f64", "p1_tan_f32", "p1_cg_f64", "p1_cg_f32",
     "p1_tanrhs_f64", "p1_tanrhs_f32", "p2_f64", "p2_f32", "p4_f64", "p4_f32", "p3_f64", "p3_f32",
     "p5_plain_f64", "p5_plain_f32", "p5_dot_f64", "p5_dot_f32", "p5_rhs_f64_to_f64",
-    "p5_rhs_f64_to_f32", "p5_rhs_f32_to_f32", "constitutive_f32", "constitutive_f64",
+    "p5_rhs_f64_to_f32", "p5_rhs_f32_to_f32", "p1_plain_dd", "p2_dd", "p3_dd", "p4_dd",
+    "p5_rhs_dd_to_f32", "p5_plain_dd_to_f64", "constitutive_f32", "constitutive_f64",
     "cg_update_f32", "cg_update_f64", "newton_update_f32", "newton_update_f64", "tangent_floor",
     "tangent_average", "cg_finish_f32", "cg_finish_f64", "tangent_bounds"};
 
@@ -145,6 +146,7 @@ struct fftg_handle {
     void* spec = nullptr;
     void* tw32 = nullptr;
     void* tw64 = nullptr;
+    void* twdd = nullptr;
     double* partials = nullptr;
     CGState* cg = nullptr;       // [nf]
     NewtonDev* nd = nullptr;     // [B]
@@ -226,7 +228,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 struct Layout {
     size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p, off_eps_p_tr, off_epbar,
         off_epbar_tr, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32,
-        off_tw64, off_partials, off_cg, off_nd, off_E, off_active, off_out36, off_guard, total;
+        off_tw64, off_twdd, off_partials, off_cg, off_nd, off_E, off_active, off_out36, off_guard, total;
 };
 
 Layout make_layout(int N, int mixed, int nrhs, int B) {
@@ -264,6 +266,7 @@ Layout make_layout(int N, int mixed, int nrhs, int B) {
     L.off_spec = take(spec);
     L.off_tw32 = take((size_t)N * 8);
     L.off_tw64 = take((size_t)N * 16);
+    L.off_twdd = take((size_t)N * 16);
     L.off_partials = take(npart * 8);
     L.off_cg = take(nf * sizeof(CGState));
     L.off_nd = take(Bs * sizeof(NewtonDev));
@@ -291,6 +294,17 @@ double frob6(const double* v) {
 }  // namespace
 
 // ---------------------------------------------------------------- internals
+// FFT precision of a pass sequence
+enum : int { FFT_F32 = 0, FFT_F64 = 1, FFT_DD = 2 };
+
+// The mixed path computes its residual G sigma with double-float FFTs
+// (dd.cuh) in place of FP64 ones: about 1e-14 of ||sigma|| where FP64 gives
+// 1e-16, far below the CG roundoff floor, at a fraction of the FP64 cost on
+// this GPU. 0: FP64 FFTs.
+#ifndef FFTG_RESIDUAL_DD
+#define FFTG_RESIDUAL_DD 1
+#endif
+
 static PassArgs base_args(fftg_handle* h, bool fp64) {
     PassArgs a{};
     a.tw = fp64 ? h->tw64 : h->tw32;
@@ -357,35 +371,45 @@ static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, 
 }
 
 // Forward-project-inverse core on the spectrum buffer (P2, P3, P4).
-static int run_p234(fftg_handle* h, bool fp64, double scale, CGState* cg, int nf, const int* mask) {
-    PassArgs a = base_args(h, fp64);
+static PassArgs base_args_fft(fftg_handle* h, int prec) {
+    PassArgs a = base_args(h, prec != FFT_F32);
+    if (prec == FFT_DD) a.tw = h->twdd;
+    return a;
+}
+
+static int run_p234(fftg_handle* h, int prec, double scale, CGState* cg, int nf, const int* mask) {
+    PassArgs a = base_args_fft(h, prec);
     a.out = h->spec;
     a.cg = cg;
     a.scale = scale;
     a.active = mask;
-    CK(pass(h, fp64 ? PK_P2_F64 : PK_P2_F32, a, nf));
-    CK(pass(h, fp64 ? PK_P3_F64 : PK_P3_F32, a, nf));
-    CK(pass(h, fp64 ? PK_P4_F64 : PK_P4_F32, a, nf));
+    const PassKind k2 = prec == FFT_DD ? PK_P2_DD : prec == FFT_F64 ? PK_P2_F64 : PK_P2_F32;
+    const PassKind k3 = prec == FFT_DD ? PK_P3_DD : prec == FFT_F64 ? PK_P3_F64 : PK_P3_F32;
+    const PassKind k4 = prec == FFT_DD ? PK_P4_DD : prec == FFT_F64 ? PK_P4_F64 : PK_P4_F32;
+    CK(pass(h, k2, a, nf));
+    CK(pass(h, k3, a, nf));
+    CK(pass(h, k4, a, nf));
     return FFTG_OK;
 }
 
-// r = -G sigma (FP64 FFT) for the cells in the active mask, rounded to the
-// inner precision; x = 0.
+// r = -G sigma for the cells in the active mask (FP64 FFTs, or double-float
+// ones in the mixed path), rounded to the inner precision; x = 0.
 static int launch_residual(fftg_handle* h) {
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
-    PassArgs a = base_args(h, true);
+    const bool dd = h->mixed && FFTG_RESIDUAL_DD;
+    PassArgs a = base_args_fft(h, dd ? FFT_DD : FFT_F64);
     a.in = h->sigma;
     a.out = h->spec;
     a.active = h->active;
-    CK(pass(h, PK_P1_PLAIN_F64, a, h->B));
-    int rc = run_p234(h, true, -invN3, nullptr, h->B, h->active);
+    CK(pass(h, dd ? PK_P1_PLAIN_DD : PK_P1_PLAIN_F64, a, h->B));
+    int rc = run_p234(h, dd ? FFT_DD : FFT_F64, -invN3, nullptr, h->B, h->active);
     if (rc) return rc;
-    PassArgs b = base_args(h, true);
+    PassArgs b = base_args_fft(h, dd ? FFT_DD : FFT_F64);
     b.in = h->spec;
     b.out = h->r;
     b.cg = h->cg;
     b.active = h->active;
-    CK(pass(h, h->mixed ? PK_P5_RHS_F64_TO_F32 : PK_P5_RHS_F64_TO_F64, b, h->B));
+    CK(pass(h, dd ? PK_P5_RHS_DD_TO_F32 : h->mixed ? PK_P5_RHS_F64_TO_F32 : PK_P5_RHS_F64_TO_F64, b, h->B));
     CK(cudaMemsetAsync(h->x, 0, (size_t)h->B * 6 * h->cs * (h->mixed ? 4 : 8), h->stream));
     return FFTG_OK;
 }
@@ -404,7 +428,7 @@ static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long
     a.out = h->spec;
     a.cg = h->cg;
     CK(pass(h, f64 ? PK_P1_CG_F64 : PK_P1_CG_F32, a, nf));
-    int rc = run_p234(h, f64, invN3, h->cg, nf, nullptr);
+    int rc = run_p234(h, f64 ? FFT_F64 : FFT_F32, invN3, h->cg, nf, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
@@ -550,7 +574,7 @@ static int project_solution(fftg_handle* h, int nf, const int* active) {
     a.out = h->spec;
     a.active = active;
     CK(pass(h, PK_P1_PLAIN_F32, a, nf));
-    int rc = run_p234(h, false, invN3, nullptr, nf, active);
+    int rc = run_p234(h, FFT_F32, invN3, nullptr, nf, active);
     if (rc) return rc;
     PassArgs b = base_args(h, false);
     b.in = h->spec;
@@ -996,6 +1020,7 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     h->spec = h->ws + L.off_spec;
     h->tw32 = h->ws + L.off_tw32;
     h->tw64 = h->ws + L.off_tw64;
+    h->twdd = h->ws + L.off_twdd;
     h->partials = (double*)(h->ws + L.off_partials);
     h->cg = (CGState*)(h->ws + L.off_cg);
     h->nd = (NewtonDev*)(h->ws + L.off_nd);
@@ -1017,8 +1042,8 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
         return fail(FFTG_ENOMEM);
     }
     std::vector<double> tw64(2 * N);
-    std::vector<float> tw32(2 * N);
-    twiddles(N, tw64.data(), tw32.data());
+    std::vector<float> tw32(2 * N), twdd(4 * N);
+    twiddles(N, tw64.data(), tw32.data(), twdd.data());
     std::vector<double> m(fftg::kMatStride * nphase);
     for (int i = 0; i < nphase; ++i) fftg::pack_phase(mats[i], &m[fftg::kMatStride * i]);
     cudaStream_t s = h->stream;
@@ -1029,6 +1054,7 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     if (!ok || cudaMemcpyAsync(h->mats, m.data(), m.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw64, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw32, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->twdd, twdd.data(), twdd.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(h->eps_star, 0, (size_t)ncells * 6 * h->cs * 8, s) != cudaSuccess ||
         cudaMemsetAsync(h->eps_p, 0, (size_t)ncells * 6 * h->cs * 8, s) != cudaSuccess ||
         cudaMemsetAsync(h->epbar, 0, (size_t)ncells * h->cs * 8, s) != cudaSuccess ||
@@ -1177,7 +1203,7 @@ int fftg_tangent(fftg_handle* h, double tol_cg, double C_out[36], int* cg_iters)
     a.tangent = tg;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_TANRHS_F64 : PK_P1_TANRHS_F32, a, 6));
-    int rc = run_p234(h, f64, -invN3, nullptr, 6, nullptr);
+    int rc = run_p234(h, f64 ? FFT_F64 : FFT_F32, -invN3, nullptr, 6, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;
@@ -1269,8 +1295,10 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
 }
 
 int fftg_op_project(fftg_handle* h, int precision, const void* tau, void* out) {
-    if (!h || !tau || !out || (precision != FFTG_FP64 && precision != FFTG_MIXED)) return FFTG_EINVAL;
-    const bool f64 = precision == FFTG_FP64;
+    if (!h || !tau || !out || (precision != FFTG_FP64 && precision != FFTG_MIXED && precision != FFTG_DD))
+        return FFTG_EINVAL;
+    const int prec = precision == FFTG_FP64 ? FFT_F64 : precision == FFTG_DD ? FFT_DD : FFT_F32;
+    const bool f64 = prec != FFT_F32;  // FP64 buffers (FFTG_FP64, FFTG_DD)
     const size_t es = f64 ? 8 : 4;
     // internal scratch in the padded layout: FP64 in sigma / eps_work, FP32
     // in p / q (these hold no state between increments)
@@ -1278,16 +1306,16 @@ int fftg_op_project(fftg_handle* h, int precision, const void* tau, void* out) {
     void* out_buf = f64 ? (void*)h->eps_work : h->q;
     CK(copy_field(h, in_buf, true, tau, false, es, cudaMemcpyDeviceToDevice));
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
-    PassArgs a = base_args(h, f64);
+    PassArgs a = base_args_fft(h, prec);
     a.in = in_buf;
     a.out = h->spec;
-    CK(pass(h, f64 ? PK_P1_PLAIN_F64 : PK_P1_PLAIN_F32, a, 1));
-    int rc = run_p234(h, f64, invN3, nullptr, 1, nullptr);
+    CK(pass(h, prec == FFT_DD ? PK_P1_PLAIN_DD : f64 ? PK_P1_PLAIN_F64 : PK_P1_PLAIN_F32, a, 1));
+    int rc = run_p234(h, prec, invN3, nullptr, 1, nullptr);
     if (rc) return rc;
-    PassArgs b = base_args(h, f64);
+    PassArgs b = base_args_fft(h, prec);
     b.in = h->spec;
     b.out = out_buf;
-    CK(pass(h, f64 ? PK_P5_PLAIN_F64 : PK_P5_PLAIN_F32, b, 1));
+    CK(pass(h, prec == FFT_DD ? PK_P5_PLAIN_DD_TO_F64 : f64 ? PK_P5_PLAIN_F64 : PK_P5_PLAIN_F32, b, 1));
     CK(copy_field(h, out, false, out_buf, true, es, cudaMemcpyDeviceToDevice));
     return FFTG_OK;
 }
@@ -1325,7 +1353,7 @@ int fftg_op_matvec(fftg_handle* h, int precision, const void* p, void* q, double
     a.tangent = (const char*)h->tangent + (size_t)h->sel * 7 * h->cs * es;
     a.out = h->spec;
     CK(pass(h, f64 ? PK_P1_TAN_F64 : PK_P1_TAN_F32, a, 1));
-    int rc = run_p234(h, f64, invN3, nullptr, 1, nullptr);
+    int rc = run_p234(h, f64 ? FFT_F64 : FFT_F32, invN3, nullptr, 1, nullptr);
     if (rc) return rc;
     PassArgs b = base_args(h, f64);
     b.in = h->spec;

@@ -267,7 +267,8 @@ const char* const kFsKindNames[FSK_COUNT] = {
     "fs_p1_plain_f64", "fs_p1_plain_f32", "fs_p1_tan_f64", "fs_p1_tan_f32", "fs_p1_cg_f64", "fs_p1_cg_f32",
     "fs_p2_f64", "fs_p2_f32", "fs_p3_f64", "fs_p3_f32", "fs_p4_f64", "fs_p4_f32",
     "fs_p5_plain_f64", "fs_p5_plain_f32", "fs_p5_dot_f64", "fs_p5_dot_f32",
-    "fs_p5_rhs_f64_to_f64", "fs_p5_rhs_f64_to_f32",
+    "fs_p5_rhs_f64_to_f64", "fs_p5_rhs_f64_to_f32", "fs_p1_plain_dd", "fs_p2_dd", "fs_p3_dd", "fs_p4_dd",
+    "fs_p5_rhs_dd_to_f32", "fs_p5_plain_dd_to_f64",
     "fs_constitutive_f32", "fs_constitutive_f64", "fs_cg_update_f32", "fs_cg_update_f64",
     "fs_cg_finish_f32", "fs_cg_finish_f64", "fs_newton_update_f32", "fs_newton_update_f64"};
 
@@ -279,7 +280,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct FsLayout {
     size_t off_phase, off_lame, off_Fstar, off_Fwork, off_P, off_hgrad, off_x, off_r, off_p, off_q,
-        off_spec, off_tw32, off_tw64, off_partials, off_cg, off_dev, off_Fbar, off_guard, total;
+        off_spec, off_tw32, off_tw64, off_twdd, off_partials, off_cg, off_dev, off_Fbar, off_guard, total;
 };
 
 FsLayout fs_layout(int N, bool mixed) {
@@ -307,6 +308,7 @@ FsLayout fs_layout(int N, bool mixed) {
     L.off_spec = take(9 * (size_t)N * N * H * 16);  // FP64 complex: the residual's size
     L.off_tw32 = take((size_t)N * 8);
     L.off_tw64 = take((size_t)N * 16);
+    L.off_twdd = take((size_t)N * 16);
     L.off_partials = take(npart * 8);
     L.off_cg = take(sizeof(CGState));
     L.off_dev = take(sizeof(FsDev));
@@ -346,6 +348,7 @@ struct fftg_fs_handle {
     void* spec = nullptr;
     void* tw32 = nullptr;
     void* tw64 = nullptr;
+    void* twdd = nullptr;
     double* partials = nullptr;
     CGState* cg = nullptr;
     FsDev* dev = nullptr;
@@ -419,9 +422,18 @@ cudaError_t fs_pass(fftg_fs_handle* h, FsPassKind kind, const FsArgs& a) {
     return e;
 }
 
-FsArgs fs_args(fftg_fs_handle* h, bool fp64) {
+// FFT precision of a pass sequence
+enum : int { FFT_F32 = 0, FFT_F64 = 1, FFT_DD = 2 };
+
+// The mixed path's residual G P uses double-float FFTs of the FP64 stress
+// (as the small-strain driver does); 0: FP64 FFTs.
+#ifndef FFTG_RESIDUAL_DD
+#define FFTG_RESIDUAL_DD 1
+#endif
+
+FsArgs fs_args(fftg_fs_handle* h, int prec) {
     FsArgs a{};
-    a.tw = fp64 ? h->tw64 : h->tw32;
+    a.tw = prec == FFT_DD ? h->twdd : prec == FFT_F64 ? h->tw64 : h->tw32;
     a.partials = h->partials;
     a.cs = h->cs;
     a.phase = h->phase;
@@ -449,13 +461,13 @@ FsPointArgs point_args(fftg_fs_handle* h) {
 }
 
 // Spectrum passes P2, P3 (scale on Ghat), P4.
-int fs_p234(fftg_fs_handle* h, bool fp64, double scale, CGState* cg) {
-    FsArgs a = fs_args(h, fp64);
+int fs_p234(fftg_fs_handle* h, int prec, double scale, CGState* cg) {
+    FsArgs a = fs_args(h, prec);
     a.cg = cg;
     a.scale = scale;
-    CK(fs_pass(h, fp64 ? FK_P2_F64 : FK_P2_F32, a));
-    CK(fs_pass(h, fp64 ? FK_P3_F64 : FK_P3_F32, a));
-    CK(fs_pass(h, fp64 ? FK_P4_F64 : FK_P4_F32, a));
+    CK(fs_pass(h, prec == FFT_DD ? FK_P2_DD : prec == FFT_F64 ? FK_P2_F64 : FK_P2_F32, a));
+    CK(fs_pass(h, prec == FFT_DD ? FK_P3_DD : prec == FFT_F64 ? FK_P3_F64 : FK_P3_F32, a));
+    CK(fs_pass(h, prec == FFT_DD ? FK_P4_DD : prec == FFT_F64 ? FK_P4_F64 : FK_P4_F32, a));
     return FFTG_OK;
 }
 
@@ -476,19 +488,21 @@ int fs_constitutive(fftg_fs_handle* h, const double* F, bool write_h, CGState* c
     return FFTG_OK;
 }
 
-// r = -G P (FP64 FFT) rounded to the inner precision, CG start; x = 0.
+// r = -G P (FP64 FFTs, or double-float ones in the mixed path) rounded to
+// the inner precision, CG start; x = 0.
 int fs_residual(fftg_fs_handle* h) {
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
-    FsArgs a = fs_args(h, true);
+    const int prec = (h->mixed && FFTG_RESIDUAL_DD) ? FFT_DD : FFT_F64;
+    FsArgs a = fs_args(h, prec);
     a.in = h->P;
-    CK(fs_pass(h, FK_P1_PLAIN_F64, a));
-    int rc = fs_p234(h, true, -invN3, nullptr);
+    CK(fs_pass(h, prec == FFT_DD ? FK_P1_PLAIN_DD : FK_P1_PLAIN_F64, a));
+    int rc = fs_p234(h, prec, -invN3, nullptr);
     if (rc) return rc;
-    FsArgs b = fs_args(h, true);
+    FsArgs b = fs_args(h, prec);
     b.in = h->spec;
     b.out = h->r;
     b.cg = h->cg;
-    CK(fs_pass(h, h->mixed ? FK_P5_RHS_F64_TO_F32 : FK_P5_RHS_F64_TO_F64, b));
+    CK(fs_pass(h, prec == FFT_DD ? FK_P5_RHS_DD_TO_F32 : h->mixed ? FK_P5_RHS_F64_TO_F32 : FK_P5_RHS_F64_TO_F64, b));
     CK(cudaMemsetAsync(h->x, 0, 9 * h->cs * (h->mixed ? 4 : 8), h->stream));
     return FFTG_OK;
 }
@@ -498,15 +512,16 @@ int fs_residual(fftg_fs_handle* h) {
 int fs_cg_iteration(fftg_fs_handle* h) {
     const bool f64 = !h->mixed;
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
-    FsArgs a = fs_args(h, f64);
+    const int prec = f64 ? FFT_F64 : FFT_F32;
+    FsArgs a = fs_args(h, prec);
     a.aux = h->r;
     a.aux2 = h->p;
     a.aux3 = h->x;
     a.cg = h->cg;
     CK(fs_pass(h, f64 ? FK_P1_CG_F64 : FK_P1_CG_F32, a));
-    int rc = fs_p234(h, f64, invN3, h->cg);
+    int rc = fs_p234(h, prec, invN3, h->cg);
     if (rc) return rc;
-    FsArgs b = fs_args(h, f64);
+    FsArgs b = fs_args(h, prec);
     b.in = h->spec;
     b.out = h->q;
     b.aux = h->p;
@@ -624,12 +639,12 @@ int fs_run_cg(fftg_fs_handle* h) {
 int fs_project_solution(fftg_fs_handle* h) {
     if (!h->mixed) return FFTG_OK;
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
-    FsArgs a = fs_args(h, false);
+    FsArgs a = fs_args(h, FFT_F32);
     a.in = h->x;
     CK(fs_pass(h, FK_P1_PLAIN_F32, a));
-    int rc = fs_p234(h, false, invN3, nullptr);
+    int rc = fs_p234(h, FFT_F32, invN3, nullptr);
     if (rc) return rc;
-    FsArgs b = fs_args(h, false);
+    FsArgs b = fs_args(h, FFT_F32);
     b.in = h->spec;
     b.out = h->x;
     CK(fs_pass(h, FK_P5_PLAIN_F32, b));
@@ -735,6 +750,7 @@ int fftg_fs_create(fftg_fs_handle** out, int N, const uint8_t* phase, int nphase
     h->spec = h->ws + L.off_spec;
     h->tw32 = h->ws + L.off_tw32;
     h->tw64 = h->ws + L.off_tw64;
+    h->twdd = h->ws + L.off_twdd;
     h->partials = (double*)(h->ws + L.off_partials);
     h->cg = (CGState*)(h->ws + L.off_cg);
     h->dev = (FsDev*)(h->ws + L.off_dev);
@@ -748,8 +764,8 @@ int fftg_fs_create(fftg_fs_handle** out, int N, const uint8_t* phase, int nphase
         return FFTG_ENOMEM;
     }
     std::vector<double> tw64(2 * N), lame(2 * nphase);
-    std::vector<float> tw32(2 * N);
-    twiddles(N, tw64.data(), tw32.data());
+    std::vector<float> tw32(2 * N), twdd(4 * N);
+    twiddles(N, tw64.data(), tw32.data(), twdd.data());
     for (int i = 0; i < nphase; ++i) {
         lame[2 * i] = mats[i].lambda;
         lame[2 * i + 1] = mats[i].mu;
@@ -762,6 +778,7 @@ int fftg_fs_create(fftg_fs_handle** out, int N, const uint8_t* phase, int nphase
         cudaMemcpyAsync(h->lame, lame.data(), lame.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw64, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->tw32, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->twdd, twdd.data(), twdd.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->Fbar_dev, h->h_Fbar, 9 * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         h->last_cuda = cudaGetLastError();
@@ -890,23 +907,25 @@ int fftg_fs_get_field(fftg_fs_handle* h, int which, double* host_out) {
 }
 
 int fftg_fs_op_project(fftg_fs_handle* h, int precision, const void* A_dev, void* out_dev) {
-    if (!h || !A_dev || !out_dev || (precision != FFTG_FP64 && precision != FFTG_MIXED)) return FFTG_EINVAL;
-    const bool f64 = precision == FFTG_FP64;
+    if (!h || !A_dev || !out_dev || (precision != FFTG_FP64 && precision != FFTG_MIXED && precision != FFTG_DD))
+        return FFTG_EINVAL;
+    const int prec = precision == FFTG_FP64 ? FFT_F64 : precision == FFTG_DD ? FFT_DD : FFT_F32;
+    const bool f64 = prec != FFT_F32;  // FP64 buffers (FFTG_FP64, FFTG_DD)
     const size_t el = f64 ? 8 : 4;
-    // staged through the padded inner buffer x (FP32) or P (FP64)
+    // staged through the padded buffer P (FP64) or x (FP32)
     void* buf = f64 ? (void*)h->P : h->x;
     if (!f64 && !h->mixed) return FFTG_EINVAL;  // FP32 buffers exist only in a mixed handle
     h->P_current = false;
     CK(fs_copy(h, buf, true, A_dev, false, el, cudaMemcpyDeviceToDevice));
-    FsArgs a = fs_args(h, f64);
+    FsArgs a = fs_args(h, prec);
     a.in = buf;
-    CK(fs_pass(h, f64 ? FK_P1_PLAIN_F64 : FK_P1_PLAIN_F32, a));
-    int rc = fs_p234(h, f64, 1.0 / ((double)h->N * h->N * h->N), nullptr);
+    CK(fs_pass(h, prec == FFT_DD ? FK_P1_PLAIN_DD : f64 ? FK_P1_PLAIN_F64 : FK_P1_PLAIN_F32, a));
+    int rc = fs_p234(h, prec, 1.0 / ((double)h->N * h->N * h->N), nullptr);
     if (rc) return rc;
-    FsArgs b = fs_args(h, f64);
+    FsArgs b = fs_args(h, prec);
     b.in = h->spec;
     b.out = buf;
-    CK(fs_pass(h, f64 ? FK_P5_PLAIN_F64 : FK_P5_PLAIN_F32, b));
+    CK(fs_pass(h, prec == FFT_DD ? FK_P5_PLAIN_DD_TO_F64 : f64 ? FK_P5_PLAIN_F64 : FK_P5_PLAIN_F32, b));
     CK(fs_copy(h, out_dev, false, buf, true, el, cudaMemcpyDeviceToDevice));
     return FFTG_OK;
 }
@@ -922,14 +941,15 @@ int fftg_fs_op_matvec(fftg_fs_handle* h, int precision, const void* p_dev, void*
     if ((rc = fs_constitutive(h, h->Fstar, true, nullptr))) return rc;
     h->P_current = true;
     CK(fs_copy(h, h->p, true, p_dev, false, el, cudaMemcpyDeviceToDevice));
-    FsArgs a = fs_args(h, f64);
+    const int prec = f64 ? FFT_F64 : FFT_F32;
+    FsArgs a = fs_args(h, prec);
     a.in = h->p;
     CK(fs_pass(h, f64 ? FK_P1_TAN_F64 : FK_P1_TAN_F32, a));
-    if ((rc = fs_p234(h, f64, 1.0 / ((double)h->N * h->N * h->N), nullptr))) return rc;
+    if ((rc = fs_p234(h, prec, 1.0 / ((double)h->N * h->N * h->N), nullptr))) return rc;
     // <p, q> through the DOT pass on a scratch CG state
     fs_set_cg(h, 1.0);
     CK(cudaMemcpyAsync(h->cg, h->h_cg, sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
-    FsArgs b = fs_args(h, f64);
+    FsArgs b = fs_args(h, prec);
     b.in = h->spec;
     b.out = h->q;
     b.aux = h->p;

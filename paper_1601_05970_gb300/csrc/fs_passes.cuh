@@ -214,9 +214,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
 #pragma unroll
                 for (int c = 0; c < 9; ++c) stv<VW, T>(pp + c * cs + v0, p[c]);
             } else {
-                const T* in = (const T*)a.in;
+                using TIn = typename PlainIn<T>::type;
+                const TIn* in = (const TIn*)a.in;
 #pragma unroll
-                for (int c = 0; c < 9; ++c) ldv<VW, T>(in + c * cs + v0, p[c]);
+                for (int c = 0; c < 9; ++c) {
+                    TIn t[VW];
+                    ldv<VW, TIn>(in + c * cs + v0, t);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) p[c][e] = T(t[e]);
+                }
                 if (MODE == FS_P1_TAN) {
                     const T* hg = (const T*)a.hgrad;
 #pragma unroll
@@ -486,6 +492,8 @@ enum FsPassKind : int {
     FK_P2_F64, FK_P2_F32, FK_P3_F64, FK_P3_F32, FK_P4_F64, FK_P4_F32,
     FK_P5_PLAIN_F64, FK_P5_PLAIN_F32, FK_P5_DOT_F64, FK_P5_DOT_F32,
     FK_P5_RHS_F64_TO_F64, FK_P5_RHS_F64_TO_F32,
+    // double-float FFTs (the mixed path's residual)
+    FK_P1_PLAIN_DD, FK_P2_DD, FK_P3_DD, FK_P4_DD, FK_P5_RHS_DD_TO_F32, FK_P5_PLAIN_DD_TO_F64,
     FK_COUNT
 };
 
@@ -525,6 +533,9 @@ template <int N>
 cudaError_t run_fs_pass_n(FsPassKind kind, const FsArgs& a, cudaStream_t s) {
     using C32 = FsCfg<N, float>;
     using C64 = FsCfg<N, double>;
+    using CDD = FsCfg<N, dd>;
+    static_assert(CDD::row_blocks == C64::row_blocks && CDD::W3 == C64::W3,
+                  "double-float passes share the FP64 geometry");
     const dim3 r32(C32::row_blocks), r64(C64::row_blocks);
     const dim3 g32((C32::H + C32::W3 - 1) / C32::W3, N), g64((C64::H + C64::W3 - 1) / C64::W3, N);
     const size_t m32 = C32::smem_rows, m64 = C64::smem_rows;
@@ -549,6 +560,13 @@ cudaError_t run_fs_pass_n(FsPassKind kind, const FsArgs& a, cudaStream_t s) {
             return launch_fs(k_fs_p5<N, double, FS_P5_RHS, double>, r64, kThreads, m64, a, s);
         case FK_P5_RHS_F64_TO_F32:
             return launch_fs(k_fs_p5<N, double, FS_P5_RHS, float>, r64, kThreads, m64, a, s);
+        case FK_P1_PLAIN_DD: return launch_fs(k_fs_p1<N, dd, FS_P1_PLAIN>, r64, kThreads, m64, a, s);
+        case FK_P2_DD: return launch_fs_p24<N, dd, true>(a, s);
+        case FK_P4_DD: return launch_fs_p24<N, dd, false>(a, s);
+        case FK_P3_DD: return launch_fs(k_fs_p3<N, dd>, g64, CDD::T3, CDD::smem_p3, a, s);
+        case FK_P5_RHS_DD_TO_F32: return launch_fs(k_fs_p5<N, dd, FS_P5_RHS, float>, r64, kThreads, m64, a, s);
+        case FK_P5_PLAIN_DD_TO_F64:
+            return launch_fs(k_fs_p5<N, dd, FS_P5_PLAIN, double>, r64, kThreads, m64, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

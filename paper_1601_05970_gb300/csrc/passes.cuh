@@ -17,6 +17,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dd.cuh"
 #include "fft_core.cuh"
 
 namespace fftg {
@@ -106,6 +107,10 @@ template <>
 struct VecN<double, 2> {
     using type = double2;
 };
+template <>
+struct VecN<dd, 2> {
+    using type = float4;
+};
 
 template <int W, typename T>
 __device__ __forceinline__ void ldv(const T* p, T (&v)[W]) {
@@ -158,6 +163,17 @@ struct Cfg {
     static constexpr size_t smem_p3 = (size_t)(6 * W3 * N + N) * CS;
     static constexpr size_t smem_p24 = (size_t)(S2 * W2 * N + N) * CS;
     static constexpr int row_blocks = (N * N + R - 1) / R;
+};
+
+// Real type a plain P1 reads: the FFT type, except for double-float FFTs,
+// whose input is an FP64 field (split into hi + lo on load).
+template <typename T>
+struct PlainIn {
+    using type = T;
+};
+template <>
+struct PlainIn<dd> {
+    using type = double;
 };
 
 template <typename T>
@@ -220,7 +236,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 2) k
     const long long base = (long long)row0 * N;
     const int nel = nrows * N;
     const long long cs = a.cs;
-    const T* in = (const T*)a.in + f * a.fstride;
+    using TIn = typename PlainIn<T>::type;
+    const TIn* in = (const TIn*)a.in + f * a.fstride;
     const T* tg = (const T*)a.tangent + f * a.tstride;
     T beta = T(0), alpha = T(0);
     bool first = true;  // first CG iteration: p = r (p holds no data yet)
@@ -272,7 +289,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 2) k
                     for (int e = 0; e < VW; ++e) p[c][e] = (c == f) ? T(1) : T(0);
             } else {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) ldv<VW, T>(in + c * cs + v0, p[c]);
+                for (int c = 0; c < 6; ++c) {
+                    TIn t[VW];
+                    ldv<VW, TIn>(in + c * cs + v0, t);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) p[c][e] = T(t[e]);
+                }
             }
             if (MODE == P1_PLAIN) {
 #pragma unroll
@@ -658,6 +680,9 @@ enum PassKind : int {
     PK_P2_F64, PK_P2_F32, PK_P4_F64, PK_P4_F32, PK_P3_F64, PK_P3_F32,
     PK_P5_PLAIN_F64, PK_P5_PLAIN_F32, PK_P5_DOT_F64, PK_P5_DOT_F32,
     PK_P5_RHS_F64_TO_F64, PK_P5_RHS_F64_TO_F32, PK_P5_RHS_F32_TO_F32,
+    // double-float FFTs (the mixed path's residual): FP64 field in, FP32
+    // residual or FP64 field out
+    PK_P1_PLAIN_DD, PK_P2_DD, PK_P3_DD, PK_P4_DD, PK_P5_RHS_DD_TO_F32, PK_P5_PLAIN_DD_TO_F64,
     PK_COUNT
 };
 
@@ -684,6 +709,10 @@ template <int N>
 cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s) {
     using C32 = Cfg<N, float>;
     using C64 = Cfg<N, double>;
+    using CDD = Cfg<N, dd>;
+    static_assert(CDD::row_blocks == C64::row_blocks && CDD::W3 == C64::W3 && CDD::W2 == C64::W2 &&
+                      CDD::S2 == C64::S2,
+                  "double-float passes share the FP64 geometry");
     const dim3 r32(C32::row_blocks, 1, nf), r64(C64::row_blocks, 1, nf);
     const dim3 c32((C32::H + C32::W2 - 1) / C32::W2, (6 * N + C32::S2 - 1) / C32::S2, nf);
     const dim3 c64((C64::H + C64::W2 - 1) / C64::W2, (6 * N + C64::S2 - 1) / C64::S2, nf);
@@ -714,6 +743,13 @@ cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s)
             return launch_k(k_p5<N, double, P5_RHS, float>, r64, C64::smem_rows, a, s);
         case PK_P5_RHS_F32_TO_F32:
             return launch_k(k_p5<N, float, P5_RHS, float>, r32, C32::smem_rows, a, s);
+        case PK_P1_PLAIN_DD: return launch_k(k_p1<N, dd, P1_PLAIN>, r64, CDD::smem_rows, a, s);
+        case PK_P2_DD: return launch_k(k_p24<N, dd, true>, c64, CDD::smem_p24, a, s, CDD::T2);
+        case PK_P4_DD: return launch_k(k_p24<N, dd, false>, c64, CDD::smem_p24, a, s, CDD::T2);
+        case PK_P3_DD: return launch_k(k_p3<N, dd>, g64, CDD::smem_p3, a, s, CDD::T3);
+        case PK_P5_RHS_DD_TO_F32: return launch_k(k_p5<N, dd, P5_RHS, float>, r64, CDD::smem_rows, a, s);
+        case PK_P5_PLAIN_DD_TO_F64:
+            return launch_k(k_p5<N, dd, P5_PLAIN, double>, r64, CDD::smem_rows, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -26,6 +26,7 @@ FFTG_ECUDA = -6
 FFTG_ESTATE = -7
 FFTG_FP64 = 0
 FFTG_MIXED = 1
+FFTG_DD = 2
 FFTG_SOLVER_CG = 0
 FFTG_SOLVER_RICHARDSON = 1
 FFTG_MODEL_J2, FFTG_MODEL_NLELASTIC, FFTG_MODEL_VISCO = 0, 1, 2
@@ -336,10 +337,15 @@ class Cell:
         return out.reshape((self.N,) * 3 if which == FFTG_FIELD_EPBAR else (6,) + (self.N,) * 3)
 
     # -- operators on device tensors ---------------------------------------
-    def project(self, tau, out=None):
+    def project(self, tau, out=None, dd=False):
+        """G tau for a device tensor with 6 * N^3 elements (float64 or
+        float32); dd=True: float64 buffers, double-float FFTs."""
         import torch
         assert tau.is_cuda and tau.is_contiguous() and tau.numel() == 6 * self.V
         prec = FFTG_FP64 if tau.dtype == torch.float64 else FFTG_MIXED
+        if dd:
+            assert tau.dtype == torch.float64
+            prec = FFTG_DD
         if out is None:
             out = torch.empty_like(tau)
         check(self._lib.fftg_op_project(self.h, prec, C.c_void_p(tau.data_ptr()),
@@ -533,11 +539,15 @@ class FsCell:
         check(self._lib.fftg_fs_get_field(self.h, which, _dptr(out)), "fftg_fs_get_field")
         return out.reshape((3, 3) + (self.N,) * 3)
 
-    def project(self, A, out=None):
-        """G A for a device tensor A with 9 * N^3 elements (float64 or float32)."""
+    def project(self, A, out=None, dd=False):
+        """G A for a device tensor A with 9 * N^3 elements (float64 or
+        float32); dd=True: float64 buffers, double-float FFTs."""
         import torch
         assert A.is_cuda and A.is_contiguous() and A.numel() == 9 * self.V
         prec = FFTG_FP64 if A.dtype == torch.float64 else FFTG_MIXED
+        if dd:
+            assert A.dtype == torch.float64
+            prec = FFTG_DD
         if out is None:
             out = torch.empty_like(A)
         check(self._lib.fftg_fs_op_project(self.h, prec, C.c_void_p(A.data_ptr()),
