@@ -70,9 +70,24 @@ int fftg_fs_create(fftg_fs_handle** h, int N, const uint8_t* phase, int nphase,
 int fftg_fs_step(fftg_fs_handle* h, const double dF[9], double tol_newton, double tol_cg,
                  double P_out[9], int* newton_iters, int* cg_iters);
 
+/* 9x9 macroscopic tangent dPbar/dFbar at the committed state (not in the
+ * paper; what an FE^2 macro solver needs): C_out[9*(3i+j) + (3k+l)] =
+ * dPbar_ij / dFbar_kl. For each unit tensor E_kl, CG solves the linearised
+ * equilibrium G K x = -G (K : E_kl) to tol_cg (with the handle's precision
+ * and inner floor), and the column is the voxel mean of K : (E_kl + x).
+ * cg_iters (may be NULL) gets the CG iterations of the nine solves. */
+int fftg_fs_tangent(fftg_fs_handle* h, double tol_cg, double C_out[81], int* cg_iters);
+
 /* Diagnostics of the last increment (fields as in fftg.h; newton_norm is
  * the finite-strain Newton test above, residual ||G P|| / ||P||). */
 int fftg_fs_last_stats(fftg_fs_handle* h, fftg_stats* out);
+
+/* Checkpoint/restore of the committed state: Fbar[9] then F*[9][N^3], FP64
+ * (fftg_fs_state_bytes() bytes). set_state rejects a wrong size or a
+ * non-finite entry (FFTG_EINVAL) and then leaves the state unchanged. */
+size_t fftg_fs_state_bytes(const fftg_fs_handle* h);
+int fftg_fs_get_state(fftg_fs_handle* h, void* host_buf, size_t bytes);
+int fftg_fs_set_state(fftg_fs_handle* h, const void* host_buf, size_t bytes);
 
 /* Copy a committed field (FFTG_FS_FIELD_*) to host memory, FP64 [9][N^3]. */
 int fftg_fs_get_field(fftg_fs_handle* h, int which, double* host_out);

@@ -239,3 +239,30 @@ def solve_increment(st: State, dFbar, tol_newton, tol_cg, max_newton=50, max_cg=
         st.Fbar = Fbar
         st.Fstar = Fs
     return StepResult(Pbar, it, cgt, norms, cgs, resid, converged)
+
+
+def macro_tangent(st: State, tol_cg, max_cg=2000):
+    """9x9 macroscopic tangent dPbar/dFbar at the committed state (row major
+    pairs: C[3i+j, 3k+l] = dPbar_ij / dFbar_kl): for each unit tensor E_kl,
+    CG on G K x = -G (K : E_kl) (the linearised equilibrium with the
+    macroscopic perturbation), then column (kl) = mean(K : (E_kl + x)).
+    Returns (C, CG iterations summed over the nine solves)."""
+    res = st.material(st.Fbar, st.Fstar)
+    tan = Tangent(res)
+    shape = (3, 3) + (st.N,) * 3
+    C = np.zeros((9, 9))
+    total = 0
+    for col in range(9):
+        E = np.zeros(shape)
+        E[col // 3, col % 3] = 1.0
+        KE = tan.apply(E)
+        rhs = -project_fs(KE)
+        nKE = np.sqrt(inner(KE, KE))
+        if np.sqrt(inner(rhs, rhs)) <= ROUNDOFF_RHS * nKE:
+            x, n = np.zeros(shape), 0
+        else:
+            x, n = cg(lambda p: project_fs(tan.apply(p)), rhs, tol_cg, max_cg,
+                      floor=ROUNDOFF_RHS * nKE)
+        total += n
+        C[:, col] = tan.apply(E + x).reshape(9, -1).mean(axis=-1)
+    return C, total

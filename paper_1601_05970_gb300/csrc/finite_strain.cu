@@ -94,6 +94,7 @@ struct FsPointArgs {
     const void* p;
     const void* q;
     double* Fw;             // Newton update: F* += x
+    int unit;               // tangent kernels: the perturbed component 3k + l
 };
 
 // P = F S with E = (H + H^T + H^T H)/2 (the Green-Lagrange strain written
@@ -243,6 +244,67 @@ __global__ void __launch_bounds__(kThreads) k_fs_newton_update(FsPointArgs a) {
     if (threadIdx.x == 0) a.dev->de2 = tot[0];
 }
 
+// Macroscopic tangent, column `unit`: ||K : E_unit||^2 summed over voxels
+// gives the CG roundoff floor of the right-hand side -G (K : E_unit).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fs_tangent_floor(FsPointArgs a) {
+    const long long V = a.V, cs = a.cs;
+    const T* hg = (const T*)a.hgrad;
+    double acc = 0.0;
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+        T h[9], d[9], s[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            h[c] = hg[c * cs + v];
+            d[c] = T(c == a.unit ? 1 : 0);
+        }
+        const double* m = a.lame + 2 * a.phase[v];
+        svk_tangent_apply<T>(h, (T)m[0], (T)m[1], d, s);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc += (double)s[c] * (double)s[c];
+    }
+    double part[1] = {block_sum(acc)};
+    if (!publish_partials<1>(part, a.partials, blockIdx.x, gridDim.x, &a.dev->ticket)) return;
+    double tot[1];
+    reduce_partials<1>(a.partials, gridDim.x, &a.dev->ticket, tot);
+    if (threadIdx.x == 0) a.cg->floor2 = kRoundoffRel * kRoundoffRel * tot[0];
+}
+
+// Macroscopic tangent, column `unit`: the voxel sums of K : (E_unit + x),
+// x the solution of G K x = -G (K : E_unit); dev->sum[9].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fs_tangent_average(FsPointArgs a) {
+    const long long V = a.V, cs = a.cs;
+    const T* hg = (const T*)a.hgrad;
+    const T* x = (const T*)a.x;
+    double acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+    for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < V;
+         v += (long long)gridDim.x * kThreads) {
+        T h[9], d[9], s[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            h[c] = hg[c * cs + v];
+            d[c] = x[c * cs + v] + T(c == a.unit ? 1 : 0);
+        }
+        const double* m = a.lame + 2 * a.phase[v];
+        svk_tangent_apply<T>(h, (T)m[0], (T)m[1], d, s);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] += (double)s[c];
+    }
+    double part[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) part[c] = block_sum(acc[c]);
+    if (!publish_partials<9>(part, a.partials, blockIdx.x, gridDim.x, &a.dev->ticket)) return;
+    double tot[9];
+    reduce_partials<9>(a.partials, gridDim.x, &a.dev->ticket, tot);
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) a.dev->sum[c] = tot[c];
+}
+
 // Loop condition of the device-resident CG graph; stops after `cap` passes
 // whatever the solve reports.
 __global__ void k_fs_cg_continue(cudaGraphConditionalHandle cond, const CGState* cg, unsigned int* guard,
@@ -261,16 +323,19 @@ namespace {
 
 enum : int {
     FSK_CONSTITUTIVE_F32 = FK_COUNT, FSK_CONSTITUTIVE_F64, FSK_CG_UPDATE_F32, FSK_CG_UPDATE_F64,
-    FSK_CG_FINISH_F32, FSK_CG_FINISH_F64, FSK_NEWTON_UPDATE_F32, FSK_NEWTON_UPDATE_F64, FSK_COUNT
+    FSK_CG_FINISH_F32, FSK_CG_FINISH_F64, FSK_NEWTON_UPDATE_F32, FSK_NEWTON_UPDATE_F64, FSK_TANGENT_FLOOR,
+    FSK_TANGENT_AVERAGE, FSK_COUNT
 };
 const char* const kFsKindNames[FSK_COUNT] = {
     "fs_p1_plain_f64", "fs_p1_plain_f32", "fs_p1_tan_f64", "fs_p1_tan_f32", "fs_p1_cg_f64", "fs_p1_cg_f32",
     "fs_p2_f64", "fs_p2_f32", "fs_p3_f64", "fs_p3_f32", "fs_p4_f64", "fs_p4_f32",
     "fs_p5_plain_f64", "fs_p5_plain_f32", "fs_p5_dot_f64", "fs_p5_dot_f32",
     "fs_p5_rhs_f64_to_f64", "fs_p5_rhs_f64_to_f32", "fs_p1_plain_dd", "fs_p2_dd", "fs_p3_dd", "fs_p4_dd",
-    "fs_p5_rhs_dd_to_f32", "fs_p5_plain_dd_to_f64",
+    "fs_p5_rhs_dd_to_f32", "fs_p5_plain_dd_to_f64", "fs_p1_tanrhs_f64", "fs_p1_tanrhs_f32",
+    "fs_p5_rhs_f32_to_f32",
     "fs_constitutive_f32", "fs_constitutive_f64", "fs_cg_update_f32", "fs_cg_update_f64",
-    "fs_cg_finish_f32", "fs_cg_finish_f64", "fs_newton_update_f32", "fs_newton_update_f64"};
+    "fs_cg_finish_f32", "fs_cg_finish_f64", "fs_newton_update_f32", "fs_newton_update_f64",
+    "fs_tangent_floor", "fs_tangent_average"};
 
 // Iterations without a new minimum of <r, r> after which an FP32 inner
 // solve counts as stagnated (as in the small-strain driver).
@@ -443,11 +508,15 @@ FsArgs fs_args(fftg_fs_handle* h, int prec) {
     return a;
 }
 
+// Every buffer pointer of the handle; kernels read only the ones they use
+// (the constitutive kernel takes its inputs and outputs from its caller).
 FsPointArgs point_args(fftg_fs_handle* h) {
     FsPointArgs u{};
     u.V = h->V;
     u.cs = h->cs;
     u.Fbar = h->Fbar_dev;
+    u.Fs = h->Fstar;
+    u.hgrad = h->hgrad;
     u.phase = h->phase;
     u.lame = h->lame;
     u.dev = h->dev;
@@ -878,6 +947,59 @@ int fftg_fs_step(fftg_fs_handle* h, const double dF[9], double tol_newton, doubl
     return FFTG_OK;
 }
 
+int fftg_fs_tangent(fftg_fs_handle* h, double tol_cg, double C_out[81], int* cg_iters) {
+    if (!h || !C_out || !(tol_cg > 0)) return FFTG_EINVAL;
+    const bool f64 = !h->mixed;
+    const int prec = f64 ? FFT_F64 : FFT_F32;
+    const double tol_inner = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
+    const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    // tangent data H at the committed state
+    int rc = fs_upload_Fbar(h, h->Fbar);
+    if (rc) return rc;
+    if ((rc = fs_constitutive(h, h->Fstar, true, nullptr))) return rc;
+    h->P_current = true;
+    int total = 0;
+    for (int unit = 0; unit < 9; ++unit) {
+        fs_set_cg(h, tol_inner);
+        CK(cudaMemcpyAsync(h->cg, h->h_cg, sizeof(CGState), cudaMemcpyHostToDevice, h->stream));
+        FsPointArgs u = point_args(h);
+        u.unit = unit;
+        int slot = fs_prof_begin(h, FSK_TANGENT_FLOOR);
+        if (f64)
+            k_fs_tangent_floor<double><<<fs_point_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        else
+            k_fs_tangent_floor<float><<<fs_point_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        fs_prof_end(h, slot);
+        CK(cudaGetLastError());
+        // r = -G (K : E_unit) in the inner precision; CG start; x = 0
+        FsArgs a = fs_args(h, prec);
+        a.unit = unit;
+        CK(fs_pass(h, f64 ? FK_P1_TANRHS_F64 : FK_P1_TANRHS_F32, a));
+        if ((rc = fs_p234(h, prec, -invN3, nullptr))) return rc;
+        FsArgs b = fs_args(h, prec);
+        b.in = h->spec;
+        b.out = h->r;
+        b.cg = h->cg;
+        CK(fs_pass(h, f64 ? FK_P5_RHS_F64_TO_F64 : FK_P5_RHS_F32_TO_F32, b));
+        CK(cudaMemsetAsync(h->x, 0, 9 * h->cs * (f64 ? 8 : 4), h->stream));
+        if ((rc = fs_run_cg(h)) || (rc = fs_project_solution(h))) return rc;
+        if (h->h_cg->done == CG_BREAKDOWN) return FFTG_ENAN;
+        total += h->h_cg->it;
+        slot = fs_prof_begin(h, FSK_TANGENT_AVERAGE);
+        if (f64)
+            k_fs_tangent_average<double><<<fs_point_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        else
+            k_fs_tangent_average<float><<<fs_point_blocks(h->V), kThreads, 0, h->stream>>>(u);
+        fs_prof_end(h, slot);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h->h_dev, h->dev, sizeof(FsDev), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int r = 0; r < 9; ++r) C_out[9 * r + unit] = h->h_dev->sum[r] / (double)h->V;
+    }
+    if (cg_iters) *cg_iters = total;
+    return FFTG_OK;
+}
+
 int fftg_fs_last_stats(fftg_fs_handle* h, fftg_stats* out) {
     if (!h || !out) return FFTG_EINVAL;
     *out = h->stats;
@@ -904,6 +1026,33 @@ int fftg_fs_get_field(fftg_fs_handle* h, int which, double* host_out) {
         return FFTG_OK;
     }
     return FFTG_EINVAL;
+}
+
+size_t fftg_fs_state_bytes(const fftg_fs_handle* h) {
+    return h ? (size_t)(9 + 9 * h->V) * sizeof(double) : 0;
+}
+
+int fftg_fs_get_state(fftg_fs_handle* h, void* host_buf, size_t bytes) {
+    if (!h || !host_buf || bytes != fftg_fs_state_bytes(h)) return FFTG_EINVAL;
+    double* d = (double*)host_buf;
+    std::memcpy(d, h->Fbar, 9 * sizeof(double));
+    CK(fs_copy(h, d + 9, false, h->Fstar, true, 8, cudaMemcpyDeviceToHost));
+    CK(cudaStreamSynchronize(h->stream));
+    return FFTG_OK;
+}
+
+int fftg_fs_set_state(fftg_fs_handle* h, const void* host_buf, size_t bytes) {
+    if (!h || !host_buf || bytes != fftg_fs_state_bytes(h)) return FFTG_EINVAL;
+    const double* d = (const double*)host_buf;
+    for (size_t k = 0; k < 9 + 9 * (size_t)h->V; ++k)
+        if (!std::isfinite(d[k])) return FFTG_EINVAL;
+    CK(fs_copy(h, h->Fstar, true, d + 9, false, 8, cudaMemcpyHostToDevice));
+    int rc = fs_upload_Fbar(h, d);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(h->Fbar, d, 9 * sizeof(double));
+    h->P_current = false;
+    return FFTG_OK;
 }
 
 int fftg_fs_op_project(fftg_fs_handle* h, int precision, const void* A_dev, void* out_dev) {

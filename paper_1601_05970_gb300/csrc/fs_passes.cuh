@@ -26,7 +26,7 @@ namespace fftg {
 constexpr int kFsComp = 9;
 constexpr int kFsPairs = 5;
 
-enum : int { FS_P1_PLAIN = 0, FS_P1_TAN = 1, FS_P1_CG = 2 };
+enum : int { FS_P1_PLAIN = 0, FS_P1_TAN = 1, FS_P1_CG = 2, FS_P1_TANRHS = 3 };
 enum : int { FS_P5_PLAIN = 0, FS_P5_DOT = 1, FS_P5_RHS = 2 };
 
 struct FsArgs {
@@ -43,6 +43,7 @@ struct FsArgs {
     const void* tw;        // w_N^j, j < N, in the FFT precision
     double scale;          // P3: factor on Ghat (+-1/N^3)
     long long cs;          // component stride of the real fields (elements)
+    int unit;              // P1_TANRHS: tau = K : E_unit, E_unit the unit tensor at component unit
 };
 
 // Tuning: voxels per lane in the elementwise phases of P1 and P5 (moved as
@@ -219,11 +220,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
 #pragma unroll
                 for (int c = 0; c < 9; ++c) {
                     TIn t[VW];
-                    ldv<VW, TIn>(in + c * cs + v0, t);
+                    if (MODE == FS_P1_TANRHS) {
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) t[e] = TIn(c == a.unit ? 1 : 0);
+                    } else {
+                        ldv<VW, TIn>(in + c * cs + v0, t);
+                    }
 #pragma unroll
                     for (int e = 0; e < VW; ++e) p[c][e] = T(t[e]);
                 }
-                if (MODE == FS_P1_TAN) {
+                if (MODE == FS_P1_TAN || MODE == FS_P1_TANRHS) {
                     const T* hg = (const T*)a.hgrad;
 #pragma unroll
                     for (int c = 0; c < 9; ++c) ldv<VW, T>(hg + c * cs + v0, h[c]);
@@ -494,6 +500,8 @@ enum FsPassKind : int {
     FK_P5_RHS_F64_TO_F64, FK_P5_RHS_F64_TO_F32,
     // double-float FFTs (the mixed path's residual)
     FK_P1_PLAIN_DD, FK_P2_DD, FK_P3_DD, FK_P4_DD, FK_P5_RHS_DD_TO_F32, FK_P5_PLAIN_DD_TO_F64,
+    // right-hand sides of the macroscopic tangent
+    FK_P1_TANRHS_F64, FK_P1_TANRHS_F32, FK_P5_RHS_F32_TO_F32,
     FK_COUNT
 };
 
@@ -567,6 +575,10 @@ cudaError_t run_fs_pass_n(FsPassKind kind, const FsArgs& a, cudaStream_t s) {
         case FK_P5_RHS_DD_TO_F32: return launch_fs(k_fs_p5<N, dd, FS_P5_RHS, float>, r64, kThreads, m64, a, s);
         case FK_P5_PLAIN_DD_TO_F64:
             return launch_fs(k_fs_p5<N, dd, FS_P5_PLAIN, double>, r64, kThreads, m64, a, s);
+        case FK_P1_TANRHS_F64: return launch_fs(k_fs_p1<N, double, FS_P1_TANRHS>, r64, kThreads, m64, a, s);
+        case FK_P1_TANRHS_F32: return launch_fs(k_fs_p1<N, float, FS_P1_TANRHS>, r32, kThreads, m32, a, s);
+        case FK_P5_RHS_F32_TO_F32:
+            return launch_fs(k_fs_p5<N, float, FS_P5_RHS, float>, r32, kThreads, m32, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -163,7 +163,11 @@ SIGNATURES = {
     "fftg_fs_step": (C.c_int, [C.c_void_p, _D6, C.c_double, C.c_double, _D6,
                                C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fftg_fs_last_stats": (C.c_int, [C.c_void_p, C.POINTER(fftg_stats)]),
+    "fftg_fs_tangent": (C.c_int, [C.c_void_p, C.c_double, _D6, C.POINTER(C.c_int)]),
     "fftg_fs_get_field": (C.c_int, [C.c_void_p, C.c_int, _D6]),
+    "fftg_fs_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "fftg_fs_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fftg_fs_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "fftg_fs_op_project": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "fftg_fs_op_matvec": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, _D6]),
     "fftg_fs_profile_kinds": (C.c_int, []),
@@ -533,6 +537,26 @@ class FsCell:
                     cg_per_newton=list(s.cg_per_newton[:n]),
                     newton_norm=list(s.newton_norm[:n]), residual=list(s.residual[:n]),
                     cg_relres=list(s.cg_relres[:n]), cg_status=list(s.cg_status[:n]))
+
+    def get_state(self):
+        """Committed state: Fbar (9) then F* (9 N^3), FP64."""
+        n = self._lib.fftg_fs_state_bytes(self.h)
+        buf = np.zeros(n // 8)
+        check(self._lib.fftg_fs_get_state(self.h, buf.ctypes.data_as(C.c_void_p), n), "fftg_fs_get_state")
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.float64)
+        check(self._lib.fftg_fs_set_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes),
+              "fftg_fs_set_state")
+
+    def tangent(self, tol_cg):
+        """9x9 macroscopic tangent dPbar/dFbar at the committed state
+        (row 3i+j, column 3k+l) and the CG iterations of its nine solves."""
+        out = np.zeros(81)
+        nc = C.c_int(0)
+        check(self._lib.fftg_fs_tangent(self.h, tol_cg, _dptr(out), C.byref(nc)), "fftg_fs_tangent")
+        return out.reshape(9, 9), nc.value
 
     def field(self, which):
         out = np.zeros(9 * self.V)

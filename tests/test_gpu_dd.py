@@ -27,7 +27,7 @@ def _lib():
     fftg.load()
 
 
-@pytest.mark.parametrize("N", [15, 45])
+@pytest.mark.parametrize("N", [5, 15, 45, 81])
 def test_small_strain_projection_in_double_float(N):
     rng = np.random.default_rng(100 + N)
     tau = rng.standard_normal((6, N, N, N))
@@ -42,7 +42,7 @@ def test_small_strain_projection_in_double_float(N):
     cell.close()
 
 
-@pytest.mark.parametrize("N", [15, 45])
+@pytest.mark.parametrize("N", [15, 45, 75])
 def test_finite_strain_projection_in_double_float(N):
     rng = np.random.default_rng(200 + N)
     A = rng.standard_normal((3, 3, N, N, N))

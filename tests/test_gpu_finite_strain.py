@@ -40,7 +40,7 @@ def _spheres(N, seed=5):
     return ph
 
 
-@pytest.mark.parametrize("N", [15, 45])
+@pytest.mark.parametrize("N", [3, 15, 25, 45, 75, 81])
 def test_projection_matches_the_oracle(N):
     rng = np.random.default_rng(N)
     A = rng.standard_normal((3, 3, N, N, N))
@@ -217,3 +217,93 @@ def test_converged_state_is_in_equilibrium_at_243():
     assert np.abs(F.reshape(3, 3, -1).mean(axis=-1) - Fbar).max() <= 1e-8
     del F
     assert _equilibrium_defect(Pf) <= 1e-5
+
+
+# ------------------------------------------------------------ macro tangent
+def test_fp64_macro_tangent_matches_the_oracle():
+    N = 9
+    ph = _spheres(N)
+    st = FS.State(N, ph, MATS)
+    cell = fftg.FsCell(N, ph, MATS, precision="fp64")
+    for dF in _path(2, 2.0):
+        FS.solve_increment(st, dF, 1e-10, 1e-12)
+        cell.step(dF, 1e-10, 1e-12)
+    Cref, nref = FS.macro_tangent(st, 1e-11)
+    C, n = cell.tangent(1e-11)
+    assert np.abs(C - Cref).max() <= 1e-9 * np.abs(Cref).max()
+    assert n == nref
+    cell.close()
+
+
+def test_mixed_macro_tangent_reaches_the_fp64_result():
+    N = 15
+    ph = _spheres(N, seed=8)
+    st = FS.State(N, ph, MATS)
+    cell = fftg.FsCell(N, ph, MATS, precision="mixed")
+    for dF in _path(2, 2.0):
+        FS.solve_increment(st, dF, 1e-10, 1e-12)
+        cell.step(dF, 1e-8, 1e-8)
+    Cref, _ = FS.macro_tangent(st, 1e-11)
+    C, n = cell.tangent(1e-8)
+    assert np.abs(C - Cref).max() <= 1e-5 * np.abs(Cref).max()
+    cell.close()
+
+
+def test_macro_tangent_of_a_homogeneous_cell_is_the_local_tangent():
+    N = 27
+    cell = fftg.FsCell(N, np.zeros((N, N, N), np.uint8), MATS[:1], precision="mixed")
+    dF = np.array([[0.2, 0.1, 0.0], [0.0, -0.1, 0.05], [0.03, 0.0, 0.1]])
+    cell.step(dF, 1e-8, 1e-8)
+    C, n = cell.tangent(1e-8)
+    res = FS.svk_update((np.eye(3) + dF)[:, :, None], np.array([MATS[0][0]]), np.array([MATS[0][1]]))
+    K = FS.svk_tangent(res)[..., 0].reshape(9, 9)
+    assert n == 0
+    assert np.abs(C - K).max() <= 1e-6 * np.abs(K).max()
+    cell.close()
+
+
+def test_macro_tangent_at_243_is_symmetric_and_stiff_in_stretch():
+    # the bench workload: the homogenised tangent of a hyperelastic cell is
+    # the Hessian of its effective energy (major-symmetric). On symmetric
+    # perturbations it is positive definite at these moderate strains; the
+    # three rotational directions carry only the geometric stiffness of the
+    # stress (eigenvalues of the order of |P|, of either sign)
+    w = I.workload("fs_spheres243")
+    cell = fftg.FsCell(w["N"], w["phase"], w["mats"], precision="mixed")
+    P, _, _ = cell.step(w["dF"][0], w["tol_newton"], w["tol_cg"])
+    C, n = cell.tangent(w["tol_cg"])
+    cell.close()
+    assert n > 0
+    assert np.abs(C - C.T).max() <= 1e-4 * np.abs(C).max()
+    Q = np.zeros((9, 6))          # orthonormal basis of symmetric 3x3 tensors
+    for c, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))):
+        E = np.zeros((3, 3))
+        E[i, j] = E[j, i] = 1.0
+        Q[:, c] = E.reshape(9) / np.linalg.norm(E)
+    ev_sym = np.linalg.eigvalsh(Q.T @ (0.5 * (C + C.T)) @ Q)
+    assert ev_sym.min() > 0.1 * ev_sym.max()
+    ev = np.linalg.eigvalsh(0.5 * (C + C.T))
+    assert np.sort(np.abs(ev))[:3].max() <= 2.0 * np.abs(P).max()
+
+
+def test_checkpoint_and_restore_continue_bit_for_bit():
+    N = 15
+    ph = _spheres(N)
+    a = fftg.FsCell(N, ph, MATS, precision="mixed")
+    path = _path(3, 2.0)
+    for dF in path[:2]:
+        a.step(dF, 1e-8, 1e-8)
+    state = a.get_state()
+    assert state.size == 9 + 9 * N ** 3
+    b = fftg.FsCell(N, ph, MATS, precision="mixed")
+    bad = state.copy()
+    bad[100] = np.nan
+    with pytest.raises(fftg.FftgError):
+        b.set_state(bad)
+    b.set_state(state)
+    Pa, na, ca = a.step(path[2], 1e-8, 1e-8)
+    Pb, nb, cb = b.step(path[2], 1e-8, 1e-8)
+    assert np.array_equal(Pa, Pb) and (na, ca) == (nb, cb)
+    assert np.array_equal(a.field(fftg.FFTG_FS_FIELD_DEFGRAD), b.field(fftg.FFTG_FS_FIELD_DEFGRAD))
+    a.close()
+    b.close()

@@ -16,7 +16,11 @@ Checked against what the mathematics fixes, not against the oracle itself:
 * the small-strain limit is the pinned small-strain oracle with
   K = lambda + 2 mu/3, G = mu, with an error that falls linearly with the
   load;
-* Newton with this tangent converges quadratically.
+* Newton with this tangent converges quadratically;
+* the 9x9 macroscopic tangent equals the local tangent for a homogeneous
+  cell, the central differences of full solves (and is major-symmetric, as
+  the Hessian of the homogenised energy), and the derivative of the
+  laminate's closed form.
 """
 import numpy as np
 import pytest
@@ -239,3 +243,55 @@ def test_solution_is_objective():
         st = FS.State(N, ph, mats)
         out.append(FS.solve_increment(st, Fb - np.eye(3), 1e-12, 1e-12).P)
     assert np.abs(out[1] - R @ out[0]).max() <= 1e-10 * np.abs(out[0]).max()
+
+
+# ------------------------------------------------------------ macro tangent
+def test_macro_tangent_of_a_homogeneous_cell_is_the_local_tangent():
+    N = 5
+    st = FS.State(N, np.zeros((N, N, N), np.uint8), (I.SVK_SOFT.as_tuple(),))
+    dF = np.array([[0.2, 0.1, 0.0], [0.0, -0.1, 0.05], [0.03, 0.0, 0.1]])
+    FS.solve_increment(st, dF, 1e-12, 1e-12)
+    C, n = FS.macro_tangent(st, 1e-12)
+    res = FS.svk_update((np.eye(3) + dF)[:, :, None], np.array([LAM0]), np.array([MU0]))
+    K = FS.svk_tangent(res)[..., 0].reshape(9, 9)
+    assert np.abs(C - K).max() <= 1e-13 * np.abs(K).max() and n == 0
+
+
+def test_macro_tangent_is_the_derivative_of_the_homogenised_stress():
+    # central differences of full solves: dPbar/dFbar_kl
+    N = 9
+    ph, _, _ = I.random_spheres(N, 0.3, 7, r_min=1.5, r_max=3.0)
+    mats = tuple(m.as_tuple() for m in I.SVK_TWO_PHASE)
+    dF = np.array([[0.08, 0.05, 0.0], [0.02, -0.04, 0.03], [0.0, 0.04, 0.03]])
+    st = FS.State(N, ph, mats)
+    FS.solve_increment(st, dF, 1e-13, 1e-14)
+    C, _ = FS.macro_tangent(st, 1e-12)
+    h = 1e-5
+    Cfd = np.zeros((9, 9))
+    for col in range(9):
+        E = np.zeros((3, 3))
+        E[col // 3, col % 3] = h
+        Pp = FS.solve_increment(FS.State(N, ph, mats, Fbar=st.Fbar.copy(), Fstar=st.Fstar.copy()), E, 1e-13, 1e-14).P
+        Pm = FS.solve_increment(FS.State(N, ph, mats, Fbar=st.Fbar.copy(), Fstar=st.Fstar.copy()), -E, 1e-13, 1e-14).P
+        Cfd[:, col] = ((Pp - Pm) / (2 * h)).reshape(9)
+    assert np.abs(C - Cfd).max() <= 1e-6 * np.abs(C).max()
+    # major symmetry of the homogenised hyperelastic tangent
+    assert np.abs(C - C.T).max() <= 1e-9 * np.abs(C).max()
+
+
+def test_macro_tangent_of_the_laminate_matches_the_closed_form():
+    N, n_hard = 9, 4
+    ph = I.laminate(N, n_hard, axis=0)
+    st = FS.State(N, ph, tuple(m.as_tuple() for m in I.SVK_TWO_PHASE))
+    dF = 0.2 * np.array([[0.5, 0.4, -0.2], [0.3, -0.2, 0.25], [0.1, 0.35, 0.2]])
+    FS.solve_increment(st, dF, 1e-13, 1e-14)
+    C, _ = FS.macro_tangent(st, 1e-13)
+    h = 1e-6
+    f = n_hard / N
+    Cfd = np.zeros((9, 9))
+    for col in range(9):
+        E = np.zeros((3, 3))
+        E[col // 3, col % 3] = h
+        Cfd[:, col] = ((_laminate_closed_form(np.eye(3) + dF + E, f, I.SVK_HARD, I.SVK_SOFT)
+                        - _laminate_closed_form(np.eye(3) + dF - E, f, I.SVK_HARD, I.SVK_SOFT)) / (2 * h)).reshape(9)
+    assert np.abs(C - Cfd).max() <= 1e-6 * np.abs(C).max()
