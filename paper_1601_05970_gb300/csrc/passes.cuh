@@ -79,6 +79,23 @@ struct PassArgs {
 #define FFTG_P3_TB 1
 #endif
 
+// Double-float passes (the mixed path's residual): P3 columns per block
+// (0 = the rule in Cfg) and minimum resident blocks per SM of P1/P5 and of
+// P3. At 243^3 one block per SM for P1/P5 (more registers) took them from
+// 2.05/1.56 to 3.42/2.66 ms; three spill.
+#ifndef FFTG_DD_P3_W
+#define FFTG_DD_P3_W 0
+#endif
+#ifndef FFTG_DD_MINB
+#define FFTG_DD_MINB 2
+#endif
+#ifndef FFTG_DD_P3_MINB
+#define FFTG_DD_P3_MINB 1
+#endif
+
+template <typename T>
+constexpr bool is_dd_v = std::is_same<T, dd>::value;
+
 // Block shapes: P3 columns per block (0 = as many as fit ~100 KB of shared
 // memory, at most 32) and P1/P5 rows per block (0 = as many as fit ~50 KB,
 // at least 4).
@@ -146,7 +163,18 @@ struct Cfg {
     // voxels per lane in P1's elementwise phase (FP64: at most 2 = 16 bytes)
     static constexpr int VW = (sizeof(T) == 8 && FFTG_P1_VW > 2) ? 2 : FFTG_P1_VW;
     static constexpr int W3a = fl2(BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(BUDGET / (6 * N * CS));
-    static constexpr int W3 = (FFTG_P3_W > 0 && FFTG_P3_W < W3a) ? FFTG_P3_W : W3a;
+    // double-float P3: up to twice the shared memory, as long as the block
+    // keeps <= 512 threads (so <= 128 registers each): at 243^3 8 columns
+    // took the pass from 3.35 to 2.29 ms against 4 (the FP64 rule); 2
+    // columns 3.33 ms
+    static constexpr int WDa = fl2(2 * BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(2 * BUDGET / (6 * N * CS));
+    static constexpr int WDt = Plan<N>::N2 == 1 ? 32
+                               : (fl2(512 / (6 * Plan<N>::N2)) < fl2(512 / (2 * Plan<N>::N1))
+                                      ? fl2(512 / (6 * Plan<N>::N2))
+                                      : fl2(512 / (2 * Plan<N>::N1)));
+    static constexpr int WD = WDa < WDt ? WDa : WDt;
+    static constexpr int W3 = is_dd_v<T> ? (FFTG_DD_P3_W > 0 ? FFTG_DD_P3_W : (WD > W3a ? WD : W3a))
+                              : (FFTG_P3_W > 0 && FFTG_P3_W < W3a) ? FFTG_P3_W : W3a;
     static constexpr int W2 = (CS == 8) ? 32 : 16;                            // columns, P2/P4
     static constexpr int S2 = fl2(BUDGET / (N * W2 * CS)) > 16 ? 16 : fl2(BUDGET / (N * W2 * CS));
     static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
@@ -219,7 +247,8 @@ struct Vec16<double> {
 
 // ----------------------------------------------------------------------- P1
 template <int N, typename T, int MODE>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : 2) k_p1(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_dd_v<T> ? FFTG_DD_MINB : 2)
+    k_p1(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -455,7 +484,8 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
 // FP32 and from 7.4 to 6.2 ms in FP64).
 template <int N, typename T>
 __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T3 <= 512)
-                                                      ? (Cfg<N, T>::T3 <= 256 ? 4 : 2) : 1) k_p3(PassArgs a) {
+                                                      ? (Cfg<N, T>::T3 <= 256 ? 4 : 2)
+                                                      : is_dd_v<T> ? FFTG_DD_P3_MINB : 1) k_p3(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int H = C::H, W = C::W3, NT = C::T3;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -517,7 +547,8 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
 // T: FFT precision; TO: output real type (P5_RHS writes the CG residual r
 // in the inner precision).
 template <int N, typename T, int MODE, typename TO>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : 2) k_p5(PassArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_dd_v<T> ? FFTG_DD_MINB : 2)
+    k_p5(PassArgs a) {
     using C = Cfg<N, T>;
     constexpr int R = C::R, H = C::H;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -710,14 +741,14 @@ cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s)
     using C32 = Cfg<N, float>;
     using C64 = Cfg<N, double>;
     using CDD = Cfg<N, dd>;
-    static_assert(CDD::row_blocks == C64::row_blocks && CDD::W3 == C64::W3 && CDD::W2 == C64::W2 &&
-                      CDD::S2 == C64::S2,
-                  "double-float passes share the FP64 geometry");
+    static_assert(CDD::row_blocks == C64::row_blocks && CDD::W2 == C64::W2 && CDD::S2 == C64::S2,
+                  "double-float row and column passes share the FP64 geometry");
     const dim3 r32(C32::row_blocks, 1, nf), r64(C64::row_blocks, 1, nf);
     const dim3 c32((C32::H + C32::W2 - 1) / C32::W2, (6 * N + C32::S2 - 1) / C32::S2, nf);
     const dim3 c64((C64::H + C64::W2 - 1) / C64::W2, (6 * N + C64::S2 - 1) / C64::S2, nf);
     const dim3 g32((C32::H + C32::W3 - 1) / C32::W3, N, nf);
     const dim3 g64((C64::H + C64::W3 - 1) / C64::W3, N, nf);
+    const dim3 gdd((CDD::H + CDD::W3 - 1) / CDD::W3, N, nf);
     switch (kind) {
         case PK_P1_PLAIN_F64: return launch_k(k_p1<N, double, P1_PLAIN>, r64, C64::smem_rows, a, s);
         case PK_P1_PLAIN_F32: return launch_k(k_p1<N, float, P1_PLAIN>, r32, C32::smem_rows, a, s);
@@ -746,7 +777,7 @@ cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s)
         case PK_P1_PLAIN_DD: return launch_k(k_p1<N, dd, P1_PLAIN>, r64, CDD::smem_rows, a, s);
         case PK_P2_DD: return launch_k(k_p24<N, dd, true>, c64, CDD::smem_p24, a, s, CDD::T2);
         case PK_P4_DD: return launch_k(k_p24<N, dd, false>, c64, CDD::smem_p24, a, s, CDD::T2);
-        case PK_P3_DD: return launch_k(k_p3<N, dd>, g64, CDD::smem_p3, a, s, CDD::T3);
+        case PK_P3_DD: return launch_k(k_p3<N, dd>, gdd, CDD::smem_p3, a, s, CDD::T3);
         case PK_P5_RHS_DD_TO_F32: return launch_k(k_p5<N, dd, P5_RHS, float>, r64, CDD::smem_rows, a, s);
         case PK_P5_PLAIN_DD_TO_F64:
             return launch_k(k_p5<N, dd, P5_PLAIN, double>, r64, CDD::smem_rows, a, s);
