@@ -19,7 +19,7 @@ struct RoundOut {
     double relres = 0.0;  // final ||r|| / ||r0||
 };
 
-// One Newton iteration (constitutive, FP64 residual, CG, eps* += d eps) for
+// One Newton iteration (constitutive, residual, CG, eps* += d eps) for
 // every cell with run[cell] != 0, all in the same launches.
 int newton_round(fftg_handle* h, const int* run, double tol_inner, RoundOut* out);
 
