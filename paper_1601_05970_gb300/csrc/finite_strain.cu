@@ -2,7 +2,8 @@
 // deformation gradient in place of the strain (the extension Section 6
 // names), one cell per handle. The grid passes are those of fs_passes.cuh;
 // the pointwise kernels here evaluate St. Venant-Kirchhoff's stress, update
-// the CG vectors and apply the Newton correction. As in the small-strain
+// the CG vectors, apply the Newton correction and form the macroscopic
+// tangent's floors and averages. As in the small-strain
 // driver, every number is computed on the device and the host reads a few
 // scalars per Newton iteration.
 #include <cuda_runtime.h>

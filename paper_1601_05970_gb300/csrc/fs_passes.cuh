@@ -4,7 +4,7 @@
 // gradient-like tensor A_ij at component 3i + j, [9][cs], and a half
 // spectrum [9][N][N][H].
 //
-// The five passes are those of the small-strain path with two changes:
+// The five passes are those of the small-strain path with three changes:
 //  * nine real components share five complex FFTs per row (pairs (0,1),
 //    (2,3), (4,5), (6,7) and component 8 alone);
 //  * the projection onto gradient fields acts row by row: with n = xi/|xi|,
@@ -15,6 +15,8 @@
 //    the phase's Lame constants: K : d = d S + F dS with
 //    E = (H + H^T + H^T H)/2, S = lambda tr(E) I + 2 mu E, M = F^T d and
 //    dS = lambda tr(M) I + mu (M + M^T).
+// The mixed path's residual runs the plain passes in double-float
+// arithmetic (dd.cuh) on the FP64 stress.
 #pragma once
 
 #include "common.cuh"
