@@ -171,7 +171,7 @@ struct fftg_handle {
     };
     std::vector<CgGraph> graphs;     // small cache of instantiated CG graphs
     unsigned long long graph_clock = 0;
-    bool graphs_broken = false;      // the driver refused: use the chunked path
+    bool graphs_broken = false;      // the CUDA driver refused: use the chunked path
 
     std::vector<double> E;           // [B][6] committed
     std::vector<char> have_tangent;  // [B]

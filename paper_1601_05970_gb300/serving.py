@@ -8,7 +8,7 @@ weights. Each session follows its own proportional strain path (a seeded
 random direction), as a Gauss point under monotone macroscopic loading
 does, so its history accumulates plastic strain from request to request. One server per grid size runs its own
 worker thread and stream, so the sizes overlap on the GPU; each server's
-cell count comes from its share of the HBM budget. The driver reports solves
+cell count comes from its share of the HBM budget. `run` reports solves
 per second and latency percentiles (submit to result, on the servers'
 clock).
 """
