@@ -96,8 +96,8 @@ def test_matvec_matches_the_oracle_at_a_deformed_state():
     cell.close()
 
 
-def test_fp64_increments_match_the_oracle():
-    N = 9
+@pytest.mark.parametrize("N", [9, 25])
+def test_fp64_increments_match_the_oracle(N):
     ph = _spheres(N)
     st = FS.State(N, ph, MATS)
     cell = fftg.FsCell(N, ph, MATS, precision="fp64")
@@ -307,3 +307,23 @@ def test_checkpoint_and_restore_continue_bit_for_bit():
     assert np.array_equal(a.field(fftg.FFTG_FS_FIELD_DEFGRAD), b.field(fftg.FFTG_FS_FIELD_DEFGRAD))
     a.close()
     b.close()
+
+
+def test_mixed_long_path_stays_on_the_oracle():
+    # ten increments to F11 = 1.3 (F12 = 0.15): the FP32 inner solves must
+    # not let the mixed state drift from the FP64 solution
+    N = 15
+    ph = _spheres(N, seed=4)
+    st = FS.State(N, ph, MATS)
+    cell = fftg.FsCell(N, ph, MATS, precision="mixed")
+    worst = 0.0
+    for dF in 3.0 * I.stretch_shear_path(10):
+        r = FS.solve_increment(st, dF, 1e-9, 1e-11)
+        P, nn, nc = cell.step(dF, 1e-8, 1e-8)
+        assert r.converged
+        worst = max(worst, np.abs(P - r.P).max() / np.abs(r.P).max())
+    F = cell.field(fftg.FFTG_FS_FIELD_DEFGRAD)
+    Fo = st.Fstar + st.Fbar[:, :, None, None, None]
+    assert worst <= 1e-7
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo - np.eye(3)[:, :, None, None, None]) <= 1e-6
+    cell.close()
