@@ -58,7 +58,9 @@ struct FsArgs {
 // blocks per SM alike; 4 spills a little) and P5 0.34 ms with 4 blocks per
 // SM (0.39 ms with 3); two voxels per lane 0.73-0.91 ms for P1 (it spills
 // at 3 blocks per SM); 80 KB of rows 0.76 ms; P3 with 100 or 64 KB of
-// columns 0.44 and 0.71 ms against 0.39 ms with 150 KB.
+// columns 0.44 and 0.71 ms against 0.39 ms with 150 KB. P5 with the
+// spectrum loads of two rounds issued together: 0.323 against 0.336 ms
+// (with 3 blocks per SM 0.369 ms).
 #ifndef FFTG_FS_VW
 #define FFTG_FS_VW 1
 #endif
@@ -73,6 +75,9 @@ struct FsArgs {
 #endif
 #ifndef FFTG_FS_P5_MINB
 #define FFTG_FS_P5_MINB 4
+#endif
+#ifndef FFTG_FS_P5_LDB
+#define FFTG_FS_P5_LDB 2
 #endif
 
 template <int N, typename T>
@@ -403,17 +408,40 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
     const int nel = nrows * N;
     const cplx<T>* in = (const cplx<T>*)a.in;
     const long long HS = (long long)N * N * H;
-    for (int it = tid; it < nrows * H; it += kThreads) {
-        const int row = it / H, k = it - row * H;
-        const long long o = (long long)(row0 + row) * H + k;
-        const int pk = perm_pos<N>(k);
-        const int pn = perm_pos<N>(k == 0 ? 0 : N - k);
+    // Spectrum rows -> tile, the loads of FFTG_FS_P5_LDB rounds issued
+    // before their stores.
+    constexpr int NRL = (R * H + kThreads - 1) / kThreads;
+    constexpr int LB = FFTG_FS_P5_LDB < NRL ? FFTG_FS_P5_LDB : NRL;
 #pragma unroll
-        for (int c = 0; c < kFsPairs; ++c) {
-            const cplx<T> a0 = in[(2 * c) * HS + o];
-            const cplx<T> b0 = (2 * c + 1 < kFsComp) ? in[(2 * c + 1) * HS + o] : mk(T(0), T(0));
-            z[(c * R + row) * N + pk] = mk(a0.x - b0.y, a0.y + b0.x);                  // A + iB
-            if (k > 0) z[(c * R + row) * N + pn] = mk(a0.x + b0.y, b0.x - a0.y);  // conj(A) + i conj(B)
+    for (int r0 = 0; r0 < NRL; r0 += LB) {
+        cplx<T> A[LB][kFsPairs], B[LB][kFsPairs];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int it = tid + (r0 + u) * kThreads;
+            if (r0 + u < NRL && it < nrows * H) {
+                const int row = it / H, k = it - row * H;
+                const long long o = (long long)(row0 + row) * H + k;
+#pragma unroll
+                for (int c = 0; c < kFsPairs; ++c) {
+                    A[u][c] = in[(2 * c) * HS + o];
+                    B[u][c] = (2 * c + 1 < kFsComp) ? in[(2 * c + 1) * HS + o] : mk(T(0), T(0));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int it = tid + (r0 + u) * kThreads;
+            if (r0 + u < NRL && it < nrows * H) {
+                const int row = it / H, k = it - row * H;
+                const int pk = perm_pos<N>(k);
+                const int pn = perm_pos<N>(k == 0 ? 0 : N - k);
+#pragma unroll
+                for (int c = 0; c < kFsPairs; ++c) {
+                    const cplx<T> a0 = A[u][c], b0 = B[u][c];
+                    z[(c * R + row) * N + pk] = mk(a0.x - b0.y, a0.y + b0.x);                  // A + iB
+                    if (k > 0) z[(c * R + row) * N + pn] = mk(a0.x + b0.y, b0.x - a0.y);  // conj(A) + i conj(B)
+                }
+            }
         }
     }
     __syncthreads();
