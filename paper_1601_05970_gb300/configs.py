@@ -1,6 +1,6 @@
 """Full runs of the five workload configurations, printed as one JSON line.
 
-    python -m paper_1601_05970_gb300.configs [--skip 4,5]
+    python -m paper_1601_05970_gb300.configs [--skip 4,5] [--only 6]
 
 1. 15^3 laminate, FP64 and mixed, shear to 0.02 in 10 increments: the
    homogenised shear stress against the closed form of the laminate (both
@@ -12,6 +12,9 @@
    increments, then the 6x6 macroscopic tangent.
 4. 256 RVEs of mixed sizes, 5 increments each (serving.run_batched).
 5. The serving loop at 50 and 100 requests/s (serving.run).
+6. Finite strain: the 45^3 laminate (FP64 and mixed) at 30 % deformation
+   against its two-layer closed form, then the 243^3 spheres stretch-shear
+   path (5 increments, mixed) and the 9x9 macroscopic tangent.
 """
 from __future__ import annotations
 
@@ -104,11 +107,62 @@ def config3():
     return out
 
 
+def _svk_P(F, lam, mu):
+    """First Piola-Kirchhoff stress of St. Venant-Kirchhoff, P = F S."""
+    E = 0.5 * (F.T @ F - np.eye(3))
+    return F @ (lam * np.trace(E) * np.eye(3) + 2.0 * mu * E)
+
+
+def _laminate_fs_closed_form(Fbar, f_h, hard, soft):
+    """Mean P of two layers normal to e1: F_k = Fbar + a_k (x) e1 with
+    f_h a_h + (1 - f_h) a_s = 0 and P e1 continuous across the interface."""
+    from scipy.optimize import fsolve
+
+    def P_of(a, m):
+        return _svk_P(Fbar + np.outer(a, [1.0, 0.0, 0.0]), m.lam, m.mu)
+
+    def resid(a_h):
+        return (P_of(a_h, hard) - P_of(-f_h / (1.0 - f_h) * a_h, soft))[:, 0]
+
+    a_h = fsolve(resid, np.zeros(3), xtol=1e-15)
+    return f_h * P_of(a_h, hard) + (1.0 - f_h) * P_of(-f_h / (1.0 - f_h) * a_h, soft)
+
+
+def config6():
+    import torch
+    from . import fftg, inputs as I
+    out = {}
+    N, n_h = 45, 17
+    dF = 0.3 * np.array([[0.5, 0.4, -0.2], [0.3, -0.2, 0.25], [0.1, 0.35, 0.2]])
+    P_ref = _laminate_fs_closed_form(np.eye(3) + dF, n_h / N, I.SVK_HARD, I.SVK_SOFT)
+    for prec, tn, tc in (("fp64", 1e-10, 1e-12), ("mixed", 1e-8, 1e-8)):
+        cell = fftg.FsCell(N, I.laminate(N, n_h, axis=0), I.SVK_TWO_PHASE, precision=prec)
+        P, nn, nc = cell.step(dF, tn, tc)
+        out[f"laminate45_{prec}"] = dict(max_rel_err_P=float(np.abs(P - P_ref).max() / np.abs(P_ref).max()),
+                                         newton=nn, cg=nc)
+        cell.close()
+    w = I.workload("fs_spheres243")
+    cell = fftg.FsCell(243, w["phase"], w["mats"], precision="mixed")
+    t, nn, nc, P = _timed_path(cell, w["dF"][:5], w["tol_newton"], w["tol_cg"])
+    t1 = time.perf_counter()
+    C, ntc = cell.tangent(w["tol_cg"])
+    torch.cuda.synchronize()
+    out["spheres243"] = dict(path_seconds=t, increments=5, newton=nn, cg=nc,
+                             P=np.asarray(P).reshape(-1).tolist(),
+                             tangent_seconds=time.perf_counter() - t1, tangent_cg=ntc,
+                             tangent_asymmetry=float(np.abs(C - C.T).max() / np.abs(C).max()))
+    cell.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--skip", default="", help="comma-separated configurations to leave out")
+    ap.add_argument("--only", default="", help="comma-separated configurations to run (default: all)")
     args = ap.parse_args(argv)
     skip = {int(s) for s in args.skip.split(",") if s}
+    if args.only:
+        skip = set(range(1, 7)) - {int(s) for s in args.only.split(",") if s}
     out = {}
     if 1 not in skip:
         out["config1"] = config1()
@@ -122,6 +176,8 @@ def main(argv=None):
             out["config4"] = serving.run_batched(serving.batched_workload())
         if 5 not in skip:
             out["config5"] = [serving.run(rate, 10.0, budget_gb=48.0) for rate in (50.0, 100.0)]
+    if 6 not in skip:
+        out["config6"] = config6()
     print(json.dumps(out))
 
 
