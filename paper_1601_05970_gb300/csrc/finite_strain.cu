@@ -1018,7 +1018,8 @@ int fftg_fs_get_field(fftg_fs_handle* h, int which, double* host_out) {
     }
     if (which == FFTG_FS_FIELD_STRESS) {
         if (!h->P_current) {
-            int rc = fs_constitutive(h, h->Fstar, false, nullptr);
+            int rc = fs_upload_Fbar(h, h->Fbar);  // the committed Fbar
+            if (rc == FFTG_OK) rc = fs_constitutive(h, h->Fstar, false, nullptr);
             if (rc) return rc;
             h->P_current = true;
         }
