@@ -58,7 +58,9 @@ _GHAT_CACHE = {}
 
 def ghat_fs_field(N: int) -> np.ndarray:
     """Ghat_fs at every frequency of an N^3 grid, [3, 3, 3, 3, N, N, N]
-    (frequency index (a, b, c) of axes (x1, x2, x3))."""
+    (frequency index (a, b, c) of axes (x1, x2, x3)). The explicit array
+    holds 81 N^3 doubles (cached per N): meant for the small grids of the
+    tests (N <= 45 takes 60 MB)."""
     if N not in _GHAT_CACHE:
         k = frequencies(N)
         xi = np.stack(np.meshgrid(k, k, k, indexing="ij"))          # [3, N, N, N]
