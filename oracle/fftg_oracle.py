@@ -10,7 +10,12 @@ over voxels but otherwise in the order the paper states it:
 * grid and frequencies ............ Section 2.3 (reduced index set, odd N)
 * DFT pair F, F^-1 ................ Eq. (DFT_forward_inverse); numpy's FFT is
                                     the library primitive, scaled to the
-                                    paper's convention (1/|N| on the forward)
+                                    paper's convention (1/|N| on the forward);
+                                    a textbook mixed-radix Cooley-Tukey FFT
+                                    (`fft_textbook`) written from the DFT sum
+                                    can replace it (FFT_IMPL = "textbook") and
+                                    pins it beyond the sizes a dense DFT
+                                    reaches
 * projection G = F^-1 Ghat F ...... Eq. (discrete_projection), Ghat from the
                                     closed form of Appendix A, Eq. (FT_projection)
 * reference-medium Green operator . Appendix A, Eq. (Gamma_explicit), used only
@@ -87,15 +92,79 @@ def frequencies(N: int) -> np.ndarray:
     return np.where(j <= (N - 1) // 2, j, j - N)
 
 
+# Which FFT evaluates the DFT sums: "library" (numpy's pocketfft, the
+# default: about ten times faster, which the full-size parity tests need) or
+# "textbook" (`fft_textbook` below). Both compute the same sums.
+FFT_IMPL = "library"
+
+
+def _smallest_factor(n: int) -> int:
+    f = 2
+    while f * f <= n:
+        if n % f == 0:
+            return f
+        f += 1
+    return n
+
+
+def _cooley_tukey(x, sign):
+    """DFT X[k] = sum_n x[n] exp(sign 2 pi i n k / N) along the last axis,
+    N = x.shape[-1], by recursive decimation in time over the smallest prime
+    factor p of N (N = p m):
+
+      n = j + p n1 (j < p, n1 < m), k = k1 + m k2 (k1 < m, k2 < p):
+      X[k1 + m k2] = sum_j w_p^(j k2) [w_N^(j k1) Y_j[k1]],
+      Y_j = the m-point DFT of the subsequence x[j + p n1],
+
+    w_L = exp(sign 2 pi i / L); a prime length is summed directly."""
+    N = x.shape[-1]
+    if N == 1:
+        return x.copy()
+    p = _smallest_factor(N)
+    if p == N:
+        n = np.arange(N)
+        W = np.exp(sign * 2j * np.pi * np.outer(n, n) / N)
+        return x @ W.T
+    m = N // p
+    # [..., j, n1] = x[j + p n1]
+    sub = np.swapaxes(x.reshape(x.shape[:-1] + (m, p)), -1, -2)
+    Y = _cooley_tukey(np.ascontiguousarray(sub), sign)
+    j = np.arange(p)
+    Y = Y * np.exp(sign * 2j * np.pi * np.outer(j, np.arange(m)) / N)
+    Wp = np.exp(sign * 2j * np.pi * np.outer(j, j) / p)
+    X = np.empty_like(Y)
+    for k2 in range(p):
+        acc = Y[..., 0, :].copy()
+        for jj in range(1, p):
+            acc += Wp[k2, jj] * Y[..., jj, :]
+        X[..., k2, :] = acc
+    return X.reshape(x.shape)
+
+
+def fft_textbook(x, axes=(-3, -2, -1), sign=-1):
+    """Unscaled multi-dimensional DFT, sum_n x[n] exp(sign 2 pi i n.k / N)
+    over `axes`, one axis at a time with the mixed-radix Cooley-Tukey
+    recursion above (radices 3 and 5 for the grids of this method)."""
+    x = np.asarray(x, dtype=np.complex128)
+    for ax in axes:
+        y = np.ascontiguousarray(np.moveaxis(x, ax, -1))
+        x = np.moveaxis(_cooley_tukey(y, sign), -1, ax)
+    return x
+
+
 def dft_forward(t):
     """F: Fourier coefficients with the 1/|N| factor on the forward sum."""
     N3 = np.prod(t.shape[-3:])
+    if FFT_IMPL == "textbook":
+        return fft_textbook(t, sign=-1) / N3
     return np.fft.fftn(t, axes=(-3, -2, -1)) / N3
 
 
 def dft_inverse(th):
     """F^-1: nodal values, no factor on the inverse sum."""
     N3 = np.prod(th.shape[-3:])
+    if FFT_IMPL == "textbook":
+        return fft_textbook(th, sign=+1)
     return np.fft.ifftn(th, axes=(-3, -2, -1)) * N3
 
 
@@ -548,7 +617,7 @@ def cg(apply_A, b, tol, max_iter=2000, fixed_iters=None, floor=0.0):
 
 
 # --------------------------------------------------------------------------
-# The basic scheme (Section 3.4): Richardson's iteration with a reference
+# The basic scheme (Section 3.2): Richardson's iteration with a reference
 # medium, as a comparison solver for the same linear system
 # --------------------------------------------------------------------------
 def mandel(C):
@@ -565,7 +634,7 @@ def mandel(C):
 
 def tangent_bounds(res):
     """lambda_min and lambda_max of the local tangents over the grid
-    (Section 3.4), from the eigenvalues of each voxel's 6x6 matrix."""
+    (Section 3.2), from the eigenvalues of each voxel's 6x6 matrix."""
     V = res.epbar.size
     lo, hi = np.inf, -np.inf
     for s0 in range(0, V, Tangent.CHUNK):

@@ -18,12 +18,39 @@ def _rng(seed=0):
 
 
 # ---------------------------------------------------------------- DFT pair
-@pytest.mark.parametrize("shape", [(5, 5, 5), (3, 5, 9), (1, 1, 1), (9, 3, 5)])
-def test_dft_matches_dense_definition(shape):
+@pytest.mark.parametrize("shape", [(5, 5, 5), (3, 5, 9), (1, 1, 1), (9, 3, 5), (15, 15, 15),
+                                   (1, 1, 243), (1, 243, 1)])
+@pytest.mark.parametrize("impl", ["library", "textbook"])
+def test_dft_matches_dense_definition(shape, impl, monkeypatch):
+    # both FFTs of the oracle against the dense DFT matrix, up to 15^3 and
+    # along a 243-point axis (the benchmark's grid)
+    monkeypatch.setattr(O, "FFT_IMPL", impl)
     t = _rng(1).standard_normal((2,) + shape)
     a = O.dft_forward(t)
     b = O.dft_forward_dense(t)
     assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(b).max())
+    assert np.abs(O.dft_inverse(a).real - t).max() <= 1e-13 * np.abs(t).max()
+
+
+@pytest.mark.parametrize("n", [2, 7, 11, 12, 49])
+def test_textbook_fft_other_lengths(n):
+    # the recursion is generic in the factors (prime lengths are summed
+    # directly): compare with the DFT sum written out for a 1D signal
+    x = _rng(n).standard_normal(n) + 1j * _rng(n + 1).standard_normal(n)
+    m = np.arange(n)
+    ref = np.exp(-2j * np.pi * np.outer(m, m) / n) @ x
+    got = O.fft_textbook(x, axes=(-1,))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape", [(45, 45, 45), (3, 5, 225), (1, 135, 81)])
+def test_library_fft_matches_textbook_fft(shape):
+    # past the sizes a dense matrix reaches, the library FFT the oracle uses
+    # by default is pinned to the textbook mixed-radix recursion
+    t = _rng(4).standard_normal(shape)
+    a = np.fft.fftn(t, axes=(-3, -2, -1))
+    b = O.fft_textbook(t)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
 
 
 def test_dft_roundtrip_parseval_and_single_mode():

@@ -201,3 +201,25 @@ def test_newton_quadratic_once_plastic_set_settles():
     # the last two steps: quadratic (a linear rate of 0.1 would fail this)
     assert nn[-1] <= 200.0 * nn[-2] ** 2
     assert nn[-2] <= 200.0 * nn[-3] ** 2
+
+
+def test_increment_same_with_textbook_fft(monkeypatch):
+    # the whole Newton-CG increment with the textbook mixed-radix FFT in
+    # place of the library FFT: the same iteration counts, and the
+    # homogenised stress and the strain field within the tolerances of the
+    # FP64 parity tests (1e-10 and 1e-9: a different rounding of each FFT,
+    # carried through the CG recursions)
+    N = 9
+    ph, _, _ = I.random_spheres(N, 0.3, 7, r_min=1.5, r_max=3.0)
+    out = {}
+    for impl in ("library", "textbook"):
+        monkeypatch.setattr(O, "FFT_IMPL", impl)
+        st = O.State(N, ph, I.TWO_PHASE)
+        rs = [O.solve_increment(st, dE, 1e-6, 1e-8) for dE in I.shear_path(0.006, 3)[:2]]
+        out[impl] = (rs, st.eps_star.copy())
+    (ra, ea), (rb, eb) = out["library"], out["textbook"]
+    assert any(r.cg_iters > 0 for r in ra)
+    for a, b in zip(ra, rb):
+        assert (a.newton_iters, a.cg_iters) == (b.newton_iters, b.cg_iters)
+        assert np.abs(a.sigma - b.sigma).max() <= 1e-10 * np.abs(a.sigma).max()
+    assert np.linalg.norm(ea - eb) <= 1e-9 * np.linalg.norm(ea)
