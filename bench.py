@@ -281,7 +281,7 @@ def time_to_converged_stress(N, precisions=("mixed", "fp64"), n_inc=4, timed_fro
 
 
 def basic_scheme_line(N=135, n_inc=4, timed_from=2):
-    """The basic scheme of Section 3.4 (Richardson's iteration with the
+    """The basic scheme of Section 3.2 (Richardson's iteration with the
     reference medium (lambda_min + lambda_max)/2 I_s) against CG on the
     same cell and load path: linear-solver iterations and wall time of the
     plastic increments, mixed precision, fresh cells (no tangent)."""

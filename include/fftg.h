@@ -49,7 +49,7 @@ extern "C" {
 
 /* ---------------------------------------------------------------- precision */
 #define FFTG_SOLVER_CG 0          /* conjugate gradients (Section 2.5) */
-#define FFTG_SOLVER_RICHARDSON 1  /* basic scheme (Section 3.4), comparison only */
+#define FFTG_SOLVER_RICHARDSON 1  /* basic scheme (Section 3.2), comparison only */
 
 #define FFTG_FP64   0  /* every step in FP64 */
 #define FFTG_MIXED  1  /* FP32 inner CG (FFT, projection, tangent contraction);
@@ -131,7 +131,7 @@ typedef struct {
     int    solver;          /* linear solver of each Newton iteration (and of
                                fftg_tangent): FFTG_SOLVER_CG (default), or
                                FFTG_SOLVER_RICHARDSON, the basic scheme of
-                               Section 3.4 as a comparison: Richardson's
+                               Section 3.2 as a comparison: Richardson's
                                iteration with the reference medium
                                C_ref = (lambda_min + lambda_max)/2 I_s updated
                                at every Newton iteration from the extreme
@@ -304,9 +304,12 @@ int fftg_server_stop(fftg_server* s);
  * call cudaMalloc: the call fails while the pool holds the memory, or it
  * stalls the whole device. This call needs no handle and no workspace.
  *
- * It evaluates the material update of Section 4 at E + eps against the
- * history (eps_p, epbar); rate-dependent phases (FFTG_MODEL_VISCO, which
- * need a time step) are not accepted here (FFTG_EINVAL). It writes
+ * It evaluates the material update of the phases' models at E + eps
+ * against the history (eps_p, epbar); rate-dependent phases
+ * (FFTG_MODEL_VISCO, which need a time step) are not accepted here
+ * (FFTG_EINVAL). Every phase id in phase_dev must be < nphase: the call
+ * checks this on the device and returns FFTG_EINVAL otherwise, with the
+ * outputs unspecified (voxels with such ids get NaN). It writes
  * sigma [6][N^3] (and, where the pointers are not
  * NULL, the updated history and the compact tangent [7][N^3] in FP32
  * (FFTG_MIXED) or FP64 (FFTG_FP64): per voxel K', 2G_eff, w11, w22, w23,
@@ -316,8 +319,8 @@ int fftg_server_stop(fftg_server* s);
  * mean(sigma) in sigma_mean[6] (host). Every field is a caller device buffer
  * in the unpadded layout [6][N^3] ([N^3] for epbar and phase).
  *
- * Its scratch (block partial sums, the reduction ticket, the material table)
- * is one fixed array of about 250 KB compiled into the library, held by every
+ * Its scratch (block partial sums, the reduction ticket, the material table,
+ * the phase-id flag) is one fixed array of about 250 KB compiled into the library, held by every
  * GPU that loads it until the process exits. Limits: N <= 243, nphase <= 256;
  * larger values return FFTG_EINVAL. The first call on a device looks up the
  * array's device address (once per device, with that device current): make

@@ -335,7 +335,7 @@ static inline double* cell_field(double* base, const fftg_handle* h, int c) {
 // null) skips cells.
 static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, int cell0,
                                const double* eps, double* sigma, bool write_history, CGState* cg,
-                               bool write_tangent = true) {
+                               bool write_tangent = true, bool elastic_only = false) {
     ConstArgs a{};
     a.V = h->V;
     a.cs = h->cs;
@@ -355,6 +355,7 @@ static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, 
     a.cg = cg ? cg + cell0 : nullptr;
     a.tie = 1e-12;
     a.dt = h->opt.dt;
+    a.elastic_only = elastic_only ? 1 : 0;
     a.active = mask_dev ? mask_dev + cell0 : nullptr;
     a.cell_fields = 6 * h->cs;
     a.cell_scalar = h->cs;
@@ -1270,12 +1271,15 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
         }
         case FFTG_FIELD_STRESS: {
             // The committed plastic strain is the return-mapped one at the
-            // committed strain, so the trial stress against it is the
-            // converged stress (Phi = 0: elastic branch). The tangent of the
-            // increment is left untouched.
+            // committed strain, so the converged stress is C_e : (eps -
+            // eps_p) there: the stress update runs with the return skipped
+            // (a visco-plastic phase has no elastic range, and a second
+            // return would relax the stress again). Non-linear elastic
+            // phases have no history and are evaluated as usual. The tangent
+            // of the increment is left untouched.
             std::memcpy(h->h_E + 6 * cell, h->E.data() + 6 * cell, 6 * sizeof(double));
             CK(cudaMemcpyAsync(h->Edev + 6 * cell, h->h_E + 6 * cell, 48, cudaMemcpyHostToDevice, h->stream));
-            int rc = launch_constitutive(h, nullptr, 1, cell, h->eps_star, h->sigma, false, nullptr, false);
+            int rc = launch_constitutive(h, nullptr, 1, cell, h->eps_star, h->sigma, false, nullptr, false, true);
             if (rc) return rc;
             CK(copy_field(h, out, false, cell_field(h->sigma, h, cell), true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));

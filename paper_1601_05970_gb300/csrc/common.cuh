@@ -38,7 +38,7 @@ struct CGState {
     double alpha;
     double beta;
     double omega;    // > 0: Richardson iteration with this fixed step (the
-                     // basic scheme, Section 3.4) instead of CG; 0: CG
+                     // basic scheme, Section 3.2) instead of CG; 0: CG
     double rr_min;   // smallest <r, r> so far
     int it_min;      // iteration of rr_min
     int stag_window; // > 0: stagnation test window (set by the host)

@@ -46,6 +46,10 @@ struct ConstArgs {
     CGState* cg;             // if set: cg->floor2 from ||sigma||
     double tie;              // plastic iff Phi_trial > tie * sigma_y
     double dt;               // time step of the increment (visco-plastic phases)
+    int elastic_only;        // 1: J2 and visco-plastic phases skip the return
+                             // (sigma = C_e : (eps - eps_p), the stress of a
+                             // committed state); non-linear elastic phases
+                             // are evaluated as usual
     // Batches of cells: cell = blockIdx.y; per-cell offsets below (0 for a
     // single cell). Edev [cells][6] replaces E when set; active[cell] == 0
     // skips the cell.
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
             const bool linear = nh == 1.0;
             const double phi = seq - (sy_h + Hh * (linear ? eb_h : pow(eb_h, nh)));
             g2 = g2e;
-            if (phi > a.tie * sy) {
+            if (!a.elastic_only && phi > a.tie * sy) {
                 double inv_seq, inv_h3;
                 if (linear) {
                     // one division gives both 1/sigma_eq and 1/(3G + H)
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent_average(VecArgs a) {
         for (int k = 0; k < 36; ++k) a.out[k] = tot[k];
 }
 
-// The basic scheme (Section 3.4, Moulinec-Suquet) solves the linear system
+// The basic scheme (Section 3.2, Moulinec-Suquet) solves the linear system
 // by Richardson's iteration with the reference medium
 // C_ref = (lambda_min + lambda_max)/2 I_s, lambda the extreme eigenvalues
 // of the local tangents over the grid; with Gamma_ref = G / c for

@@ -1,4 +1,4 @@
-"""The basic scheme (Section 3.4, FFTG_SOLVER_RICHARDSON) on the GPU against
+"""The basic scheme (Section 3.2, FFTG_SOLVER_RICHARDSON) on the GPU against
 the oracle's Richardson iteration, and against the GPU's own CG.
 
 Tolerances as in the other parity tests: FP64 solves 1e-10 in the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's basic scheme (Section 3.4: Richardson's iteration
+"""Pins of the oracle's basic scheme (Section 3.2: Richardson's iteration
 with the reference medium C_ref = (lambda_min + lambda_max)/2 I_s).
 
 Checked against:
