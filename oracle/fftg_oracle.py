@@ -841,6 +841,6 @@ def solve_increment_keep(st: State, dE6, tol_newton, tol_cg, **kw):
     eps_p_prev, epbar_prev = st.eps_p.copy(), st.epbar.copy()
     r = solve_increment(st, dE6, tol_newton, tol_cg, **kw)
     tmp = State(st.N, st.phase, st.mats, E=st.E, eps_star=st.eps_star,
-                eps_p=eps_p_prev, epbar=epbar_prev)
+                eps_p=eps_p_prev, epbar=epbar_prev, dt=st.dt)
     st.last_res = tmp.constitutive(st.E, st.eps_star)
     return r

@@ -231,3 +231,24 @@ def test_paper_laminate_visco_plastic():
     assert np.abs(eps12[ph == 1] - e1).max() <= 1e-9 * E12
     assert np.abs(eps12[ph == 0] - e2).max() <= 1e-9 * E12
     assert abs(r.sigma[5] - 2.0 * G * e2) <= 1e-9 * 2.0 * G * e2
+
+
+def test_kept_final_update_of_a_visco_increment_is_the_converged_stress():
+    # solve_increment_keep evaluates the last stress update again against
+    # the previous history: with the increment's time step (Section 4.3),
+    # its stress field is the converged one, so its mean is the homogenised
+    # stress of the increment and it is the elastic stress C_e : (eps -
+    # eps_p) of the committed plastic strain
+    N, k, T, E12 = 9, 5, 0.2, 0.05
+    ph, mats = _laminate(N, 3, I.Phase(K, G, 1e9, 0.0), I.ViscoPlastic(K, G, S0V, E0V, T0V, 0.3))
+    st = O.State(N, ph, mats, dt=T / k)
+    for _ in range(2):
+        r = O.solve_increment_keep(st, np.array([0, 0, 0, 0, 0, E12 / k]), 1e-10, 1e-12)
+    sig = st.last_res.sigma
+    assert np.abs(O.to_comps(sig.reshape(3, 3, -1).mean(axis=-1)) - r.sigma).max() <= 1e-13
+    ee = st.eps_star + st.E[:, :, None, None, None] - st.eps_p
+    tr = ee[0, 0] + ee[1, 1] + ee[2, 2]
+    el = 2.0 * G * ee
+    for i in range(3):
+        el[i, i] += (K - 2.0 * G / 3.0) * tr
+    assert np.abs(el - sig).max() <= 1e-13
