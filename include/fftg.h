@@ -67,6 +67,13 @@ extern "C" {
 #define FFTG_FIELD_STRESS  1  /* stress at the committed state, [6][N^3] */
 #define FFTG_FIELD_EPBAR   2  /* accumulated plastic strain, [N^3] */
 #define FFTG_FIELD_EPS_P   3  /* plastic strain tensor, [6][N^3] */
+#define FFTG_FIELD_TANGENT 4  /* compact consistent tangent of the last stress
+                                 update (Section 4.2), [7][N^3]: K', 2G_eff,
+                                 w11, w22, w23, w13, w12, with C = |K'| I(x)I +
+                                 2G_eff I_d - sign(K') w(x)w and w33 =
+                                 -(w11 + w22); converted to FP64 from the inner
+                                 precision it is stored in (FP32 in
+                                 FFTG_MIXED). FFTG_ESTATE before any update */
 
 typedef struct fftg_handle fftg_handle;
 
@@ -224,7 +231,14 @@ size_t fftg_state_bytes(const fftg_handle* h);
 int fftg_get_state(fftg_handle* h, void* host_buf, size_t bytes);
 int fftg_set_state(fftg_handle* h, const void* host_buf, size_t bytes);
 
-/* Copy a committed field to host memory (FFTG_FIELD_*; FP64). */
+/* Reset the committed state of the selected cell to the undeformed one:
+ * E = 0, eps* = 0, no plastic history (the microstructure is kept), as if
+ * the cell had just been created; the next fftg_step starts the load path
+ * again. Keeps the handle's cached CUDA graphs. */
+int fftg_reset_state(fftg_handle* h);
+
+/* Copy a committed field to host memory (FFTG_FIELD_*; FP64), or the
+ * tangent of the last stress update (FFTG_FIELD_TANGENT). */
 int fftg_get_field(fftg_handle* h, int which, double* host_out);
 
 void fftg_destroy(fftg_handle* h);
@@ -293,6 +307,10 @@ int fftg_server_submit(fftg_server* s, long long request_id, long long session_i
 int fftg_server_poll(fftg_server* s, fftg_result* out, int max, int* n, double wait_s);
 int fftg_server_info(fftg_server* s, long long* completed, long long* evictions,
                      long long* restores, int* max_concurrent, double* mean_batch);
+/* Drops every request not yet admitted into a cell (queued ones); requests
+ * in flight complete and are reported as usual. Dropped requests produce no
+ * result. `cancelled` (may be NULL) receives their number. */
+int fftg_server_cancel_pending(fftg_server* s, long long* cancelled);
 /* Drains the queue, stops the worker and frees everything. */
 int fftg_server_stop(fftg_server* s);
 
@@ -348,6 +366,15 @@ int fftg_profile_reset(fftg_handle* h);
 int fftg_profile_read(fftg_handle* h, int kind, double* total_ms, long long* launches);
 /* Kernels this handle has launched since creation (always counted). */
 long long fftg_launch_count(const fftg_handle* h);
+
+/* Fused multiply-add throughput of the current device in TFLOP/s (2 flops
+ * per FMA), FP64 (precision FFTG_FP64) or FP32 (FFTG_MIXED): one launch of
+ * 8 blocks per SM whose threads each run 8 independent chains of `iters`
+ * FMAs, timed with CUDA events in `stream` (NULL = legacy default stream;
+ * the call synchronises it). The roofline denominator of ALU-bound passes;
+ * the paper has no counterpart. FFTG_EINVAL for iters < 8 or another
+ * precision. */
+int fftg_probe_fma_rate(int precision, int iters, void* stream, double* tflops);
 
 #ifdef __cplusplus
 }

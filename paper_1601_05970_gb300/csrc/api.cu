@@ -91,7 +91,8 @@ const char* const kKindNames[KK_COUNT] = {
     "p1_tanrhs_f64", "p1_tanrhs_f32", "p2_f64", "p2_f32", "p4_f64", "p4_f32", "p3_f64", "p3_f32",
     "p5_plain_f64", "p5_plain_f32", "p5_dot_f64", "p5_dot_f32", "p5_rhs_f64_to_f64",
     "p5_rhs_f64_to_f32", "p5_rhs_f32_to_f32", "p1_plain_dd", "p2_dd", "p3_dd", "p4_dd",
-    "p5_rhs_dd_to_f32", "p5_plain_dd_to_f64", "constitutive_f32", "constitutive_f64",
+    "p5_rhs_dd_to_f32", "p5_plain_dd_to_f64", "p1_cgf_f32", "p5_cgf_f32", "constitutive_f32",
+    "constitutive_f64",
     "cg_update_f32", "cg_update_f64", "newton_update_f32", "newton_update_f64", "tangent_floor",
     "tangent_average", "cg_finish_f32", "cg_finish_f64", "tangent_bounds"};
 
@@ -174,7 +175,8 @@ struct fftg_handle {
     bool graphs_broken = false;      // the CUDA driver refused: use the chunked path
 
     std::vector<double> E;           // [B][6] committed
-    std::vector<char> have_tangent;  // [B]
+    std::vector<char> have_tangent;  // [B] a converged increment's tangent is held
+    std::vector<char> have_update;   // [B] some stress update wrote the tangent
     std::vector<fftg_stats> stats;   // [B]
     long long launches = 0;
     Prof* prof = nullptr;
@@ -368,6 +370,9 @@ static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, 
         k_constitutive<double><<<g, kThreads, 0, h->stream>>>(a);
     prof_end(h, slot);
     CK(cudaGetLastError());
+    if (write_tangent)
+        for (int b = cell0; b < cell0 + ncells; ++b)
+            if (!mask_dev || (mask_dev == h->active && h->h_active[b])) h->have_update[b] = 1;
     return FFTG_OK;
 }
 
@@ -415,11 +420,41 @@ static int launch_residual(fftg_handle* h) {
     return FFTG_OK;
 }
 
+// The mixed path's CG (not the basic scheme) runs without the update pass:
+// alpha from <p, C : p> in P1, r -= alpha q in P5 (passes.cuh, P1_CGF).
+// 0: P1_CG / P5_DOT and the update pass, as in the FP64 path.
+#ifndef FFTG_CG_FUSED
+#define FFTG_CG_FUSED 1
+#endif
+static bool cg_fused(const fftg_handle* h) {
+    return FFTG_CG_FUSED && h->mixed && h->opt.solver == FFTG_SOLVER_CG;
+}
+
 // One CG iteration on nf fields: the fused matvec passes and the update.
 // `tangent`/`tstride`: per-field tangents (batched cells) or one shared.
 static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long long tstride) {
     const bool f64 = !h->mixed;
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
+    if (cg_fused(h)) {
+        PassArgs a = base_args(h, false);
+        a.aux = h->r;
+        a.aux2 = h->p;
+        a.aux3 = h->x;
+        a.tangent = tangent;
+        a.tstride = tstride;
+        a.out = h->spec;
+        a.cg = h->cg;
+        CK(pass(h, PK_P1_CGF_F32, a, nf));
+        int rc = run_p234(h, FFT_F32, invN3, h->cg, nf, nullptr);
+        if (rc) return rc;
+        PassArgs b = base_args(h, false);
+        b.in = h->spec;
+        b.aux = h->r;
+        b.aux3 = h->r;
+        b.cg = h->cg;
+        CK(pass(h, PK_P5_CGF_F32, b, nf));
+        return FFTG_OK;
+    }
     PassArgs a = base_args(h, f64);
     a.aux = h->r;
     a.aux2 = h->p;
@@ -651,7 +686,7 @@ static int run_cg(fftg_handle* h, int nf, const void* tangent, long long tstride
             CK(cudaStreamSynchronize(h->stream));
             int maxit = 0;
             for (int f = 0; f < nf; ++f) maxit = std::max(maxit, h->h_cg[f].it);
-            h->launches += 7LL * (maxit + 1);
+            h->launches += (cg_fused(h) ? 6LL : 7LL) * (maxit + 1);
             return FFTG_OK;
         }
         h->graphs_broken = true;
@@ -821,6 +856,7 @@ int upload_cell(fftg_handle* h, int cell, const uint8_t* phase, const double* st
         std::fill(h->E.begin() + 6 * cell, h->E.begin() + 6 * cell + 6, 0.0);
     }
     h->have_tangent[cell] = 0;
+    h->have_update[cell] = 0;
     CK(cudaStreamSynchronize(h->stream));
     return FFTG_OK;
 }
@@ -986,6 +1022,7 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     h->nphase = nphase;
     h->E.assign((size_t)6 * ncells, 0.0);
     h->have_tangent.assign(ncells, 0);
+    h->have_update.assign(ncells, 0);
     h->stats.assign(ncells, fftg_stats{});
     const Layout L = make_layout(N, h->mixed, h->nrhs, ncells);
     if (o.workspace) {
@@ -1257,6 +1294,11 @@ int fftg_set_state(fftg_handle* h, const void* buf, size_t bytes) {
     return upload_cell(h, h->sel, nullptr, d);
 }
 
+int fftg_reset_state(fftg_handle* h) {
+    if (!h) return FFTG_EINVAL;
+    return upload_cell(h, h->sel, nullptr, nullptr);
+}
+
 int fftg_get_field(fftg_handle* h, int which, double* out) {
     if (!h || !out) return FFTG_EINVAL;
     const size_t V = (size_t)h->V;
@@ -1293,6 +1335,21 @@ int fftg_get_field(fftg_handle* h, int which, double* out) {
             CK(copy_field(h, out, false, cell_field(h->eps_p, h, cell), true, 8, cudaMemcpyDeviceToHost));
             CK(cudaStreamSynchronize(h->stream));
             return FFTG_OK;
+        case FFTG_FIELD_TANGENT: {
+            if (!h->have_update[cell]) return FFTG_ESTATE;
+            const size_t ts = h->mixed ? 4 : 8;
+            const char* tg = (const char*)h->tangent + (size_t)cell * 7 * h->cs * ts;
+            if (!h->mixed) {
+                CK(copy_field(h, out, false, tg, true, 8, cudaMemcpyDeviceToHost, 7));
+                CK(cudaStreamSynchronize(h->stream));
+                return FFTG_OK;
+            }
+            std::vector<float> tmp(7 * V);
+            CK(copy_field(h, tmp.data(), false, tg, true, 4, cudaMemcpyDeviceToHost, 7));
+            CK(cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < 7 * V; ++i) out[i] = (double)tmp[i];
+            return FFTG_OK;
+        }
         default:
             return FFTG_EINVAL;
     }

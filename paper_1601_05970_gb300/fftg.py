@@ -34,6 +34,7 @@ FFTG_FIELD_STRAIN = 0
 FFTG_FIELD_STRESS = 1
 FFTG_FIELD_EPBAR = 2
 FFTG_FIELD_EPS_P = 3
+FFTG_FIELD_TANGENT = 4
 FFTG_MAX_NEWTON_LOG = 64
 FFTG_FS_FIELD_DEFGRAD = 0
 FFTG_FS_FIELD_STRESS = 1
@@ -134,6 +135,8 @@ SIGNATURES = {
     "fftg_profile_reset": (C.c_int, [C.c_void_p]),
     "fftg_profile_read": (C.c_int, [C.c_void_p, C.c_int, _D6, C.POINTER(C.c_longlong)]),
     "fftg_launch_count": (C.c_longlong, [C.c_void_p]),
+    "fftg_reset_state": (C.c_int, [C.c_void_p]),
+    "fftg_probe_fma_rate": (C.c_int, [C.c_int, C.c_int, C.c_void_p, _D6]),
     "fftg_workspace_size_batch": (C.c_int, [C.c_int, C.c_int, C.POINTER(fftg_options),
                                             C.POINTER(C.c_size_t)]),
     "fftg_create_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_uint8),
@@ -153,6 +156,7 @@ SIGNATURES = {
     "fftg_server_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_longlong), C.POINTER(C.c_int), _D6]),
     "fftg_server_stop": (C.c_int, [C.c_void_p]),
+    "fftg_server_cancel_pending": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "fftg_constitutive_noalloc": (C.c_int, [C.c_int, _D6, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_int, C.POINTER(fftg_phase), C.c_int,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _D6,
@@ -323,6 +327,9 @@ class Cell:
         return out.reshape(6, 6), nc.value
 
     # -- state --------------------------------------------------------------
+    def reset_state(self):
+        check(self._lib.fftg_reset_state(self.h), "fftg_reset_state")
+
     def get_state(self):
         n = self._lib.fftg_state_bytes(self.h)
         buf = np.zeros(n // 8)
@@ -335,10 +342,10 @@ class Cell:
               "fftg_set_state")
 
     def field(self, which):
-        n = self.V if which == FFTG_FIELD_EPBAR else 6 * self.V
-        out = np.zeros(n)
+        nc = {FFTG_FIELD_EPBAR: 1, FFTG_FIELD_TANGENT: 7}.get(which, 6)
+        out = np.zeros(nc * self.V)
         check(self._lib.fftg_get_field(self.h, which, _dptr(out)), "fftg_get_field")
-        return out.reshape((self.N,) * 3 if which == FFTG_FIELD_EPBAR else (6,) + (self.N,) * 3)
+        return out.reshape((self.N,) * 3 if nc == 1 else (nc,) + (self.N,) * 3)
 
     # -- operators on device tensors ---------------------------------------
     def project(self, tau, out=None, dd=False):
@@ -449,6 +456,12 @@ class Server:
                             newton_iters=r.newton_iters, cg_iters=r.cg_iters, sigma=list(r.sigma),
                             t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done))
         return out
+
+    def cancel_pending(self):
+        """Drop the requests not yet admitted; returns how many."""
+        n = C.c_longlong(0)
+        check(self._lib.fftg_server_cancel_pending(self.h, C.byref(n)), "fftg_server_cancel_pending")
+        return n.value
 
     def info(self):
         c, e, r = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
@@ -606,3 +619,14 @@ class FsCell:
 
     def launches(self):
         return int(self._lib.fftg_fs_launch_count(self.h))
+
+
+def fma_rate(precision="fp64", iters=1 << 16, stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s (FP64 or
+    FP32), by the library's probe kernel (fftg_probe_fma_rate)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double(0.0)
+    check(load().fftg_probe_fma_rate(FFTG_FP64 if precision == "fp64" else FFTG_MIXED, int(iters),
+                                     C.c_void_p(st.cuda_stream), C.byref(out)), "fftg_probe_fma_rate")
+    return out.value
