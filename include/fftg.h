@@ -271,6 +271,32 @@ int fftg_op_constitutive(fftg_handle* h, const double dE[6], const double* eps_d
 int fftg_op_matvec(fftg_handle* h, int precision, const void* p_dev, void* q_dev,
                    double* pq);
 
+/* ---------------------------------------------------------------- groups
+ * One increment of every cell of several batch handles (cells of several
+ * grid sizes) as ONE CUDA graph launch: per handle a branch of the graph
+ * runs Algorithm 1's Newton loop and each Newton iteration's CG loop as
+ * device-side WHILE loops (conditional graph nodes), with the Newton test
+ * taken per cell on the device, then commits the converged cells; the
+ * branches of different handles run concurrently. The results are those of
+ * fftg_batch_step on each handle (the same kernels in the same order). The
+ * graph is built at the first step and again when the tolerances change;
+ * it holds the handles' buffers, so the handles must outlive the group and
+ * not be used on their own streams while a group step runs (the call
+ * synchronises them first). Handles must use the CG solver (not the basic
+ * scheme). Not in the paper: it serves the FE^2 setting of Section 1, where
+ * many RVEs of different sizes take one increment per macroscopic step. */
+typedef struct fftg_group fftg_group;
+int fftg_group_create(fftg_group** g, fftg_handle* const* handles, int n);
+/* dE, run, sigma_out, newton_iters, cg_iters, status: the cells of all
+ * handles in group order ([sum of batch sizes][6] or [sum of batch sizes]);
+ * run may be NULL (every cell runs); newton_iters and cg_iters may be NULL.
+ * Returns the first failing cell's status (others are still reported). */
+int fftg_group_step(fftg_group* g, const double* dE, const int* run, double tol_newton, double tol_cg,
+                    double* sigma_out, int* newton_iters, int* cg_iters, int* status);
+/* Kernel launches the group's graphs made (counted from the iterations). */
+long long fftg_group_launch_count(const fftg_group* g);
+void fftg_group_destroy(fftg_group* g);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching of RVE increments (not in the paper; the FE^2 use of
  * Section 1: a macro solver issues one strain increment per Gauss point).
@@ -366,6 +392,45 @@ int fftg_profile_reset(fftg_handle* h);
 int fftg_profile_read(fftg_handle* h, int kind, double* total_ms, long long* launches);
 /* Kernels this handle has launched since creation (always counted). */
 long long fftg_launch_count(const fftg_handle* h);
+
+/* ---------------------------------------------------------------- schedules
+ * The FP32 passes of the mixed CG iteration run one of FFTG_SCHED_VARIANTS
+ * schedules per grid size and pass: the radix split of the pencil transform
+ * (the default split or the other one, e.g. 27 x 9 or 9 x 27 at N = 243)
+ * and the tile (rows per block of P1/P5, columns per block of P2-P4).
+ * Every schedule computes the same transforms (results agree to FP32
+ * rounding). The choice is process-wide per grid size and applies to
+ * launches enqueued afterwards; a handle's CUDA graphs keep the kernels they
+ * captured, so set or tune schedules before creating the handles that should
+ * use them. Not part of the paper's method. */
+#define FFTG_SCHED_P1 0        /* x3 transform + C : p (CG)            */
+#define FFTG_SCHED_P2 1        /* x2 transform                          */
+#define FFTG_SCHED_P3 2        /* x1 transform + Ghat + inverse          */
+#define FFTG_SCHED_P4 3        /* inverse x2 transform                  */
+#define FFTG_SCHED_P5 4        /* inverse x3 transform + r update (CG)  */
+#define FFTG_SCHED_KINDS 5
+#define FFTG_SCHED_VARIANTS 4
+#define FFTG_TUNE_CACHE 1      /* read and write the schedule cache file */
+#define FFTG_TUNE_FORCE 2      /* time again even when the cache has the grid */
+/* Select schedule `variant` (0 = default) of pass `kind` at grid N. */
+int fftg_schedule_set(int N, int kind, int variant);
+/* The variant in use, or FFTG_EINVAL. */
+int fftg_schedule_get(int N, int kind);
+/* shape[5]: radix split n1, n2; rows per block; columns per block; blocks
+ * per field of the launch. */
+int fftg_schedule_describe(int N, int kind, int variant, int shape[5]);
+/* Times every variant of every kind at grid N on one field of scratch
+ * device memory (cudaMalloc'd for the call, about 170 B per voxel) in
+ * `stream` (synchronised), and selects the fastest of each kind (a variant
+ * replaces the default only when at least 2 % faster). ms (may be NULL):
+ * [FFTG_SCHED_KINDS][FFTG_SCHED_VARIANTS] median milliseconds, -1 when the
+ * cache supplied the choice; chosen[FFTG_SCHED_KINDS]. With FFTG_TUNE_CACHE
+ * the choices are read from / appended to the cache file
+ * $FFTG_SCHEDULE_CACHE (default $XDG_CACHE_HOME/fftg/schedules.txt, else
+ * ~/.cache/fftg/schedules.txt), keyed by device name, grid size and library
+ * build, and a grid found there is not timed again (unless FFTG_TUNE_FORCE).
+ * Thread-safe against itself; not against solves running meanwhile. */
+int fftg_autotune(int N, int flags, void* stream, double* ms, int* chosen);
 
 /* Fused multiply-add throughput of the current device in TFLOP/s (2 flops
  * per FMA), FP64 (precision FFTG_FP64) or FP32 (FFTG_MIXED): one launch of

@@ -66,6 +66,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                        os.path.join(CSRC, "passes_inst.cu"), "-o",
                        os.path.join(BUILD, f"passes_{n}.o")]))
         units.append(([nvcc] + ARCH + FLAGS + [f"-DFFTG_N={n}", "-c",
+                       os.path.join(CSRC, "passes_tune.cu"), "-o",
+                       os.path.join(BUILD, f"tune_{n}.o")]))
+        units.append(([nvcc] + ARCH + FLAGS + [f"-DFFTG_N={n}", "-c",
                        os.path.join(CSRC, "fs_inst.cu"), "-o",
                        os.path.join(BUILD, f"fs_{n}.o")]))
     units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "finite_strain.cu"), "-o",
@@ -76,14 +79,22 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                                           os.path.join(BUILD, "noalloc.o")])
     units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "server.cu"), "-o",
                                           os.path.join(BUILD, "server.o")])
+    units.append([nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, "probe.cu"), "-o",
+                                          os.path.join(BUILD, "probe.o")])
+    # the schedule cache is keyed by this build's source digest
+    units.append([nvcc] + ARCH + FLAGS + [f'-DFFTG_BUILD_ID="{digest[:16]}"', "-c",
+                                          os.path.join(CSRC, "autotune.cu"), "-o",
+                                          os.path.join(BUILD, "autotune.o")])
     logs = []
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         for out in ex.map(_run, units):
             logs.append(out)
     objs = ([os.path.join(BUILD, f"passes_{n}.o") for n in GRIDS]
+            + [os.path.join(BUILD, f"tune_{n}.o") for n in GRIDS]
             + [os.path.join(BUILD, f"fs_{n}.o") for n in GRIDS]
             + [os.path.join(BUILD, "finite_strain.o"), os.path.join(BUILD, "api.o"), os.path.join(BUILD, "noalloc.o"),
-               os.path.join(BUILD, "server.o")])
+               os.path.join(BUILD, "server.o"), os.path.join(BUILD, "probe.o"),
+               os.path.join(BUILD, "autotune.o")])
     tmp = LIB + ".tmp"
     _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
     os.replace(tmp, LIB)

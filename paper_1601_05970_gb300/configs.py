@@ -11,7 +11,7 @@
 3. 243^3 spheres (hard fraction 0.2), uniaxial strain to 0.03 in 20
    increments, then the 6x6 macroscopic tangent.
 4. 256 RVEs of mixed sizes, 5 increments each (serving.run_batched).
-5. The serving loop at 50 and 100 requests/s (serving.run).
+5. The serving loop at 50, 100, 200 and 500 requests/s (serving.run).
 6. Finite strain: the 45^3 laminate (FP64 and mixed) at 30 % deformation
    against its two-layer closed form, then the 243^3 spheres stretch-shear
    path (5 increments, mixed) and the 9x9 macroscopic tangent.
@@ -175,7 +175,7 @@ def main(argv=None):
         if 4 not in skip:
             out["config4"] = serving.run_batched(serving.batched_workload())
         if 5 not in skip:
-            out["config5"] = [serving.run(rate, 10.0, budget_gb=48.0) for rate in (50.0, 100.0)]
+            out["config5"] = [serving.run(rate, 10.0) for rate in (50.0, 100.0, 200.0, 500.0)]
     if 6 not in skip:
         out["config6"] = config6()
     print(json.dumps(out))

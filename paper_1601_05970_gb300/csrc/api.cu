@@ -21,6 +21,8 @@
 #include "materials.h"
 #include "passes.cuh"
 #include "pointwise.cuh"
+#include "schedule.cuh"
+#include "batch.cuh"
 
 namespace fftg {
 #define FFTG_EXTERN_N(n) extern template cudaError_t run_pass_n<n>(PassKind, const PassArgs&, int, cudaStream_t);
@@ -42,6 +44,11 @@ FFTG_EXTERN_N(243)
 static bool supported_n(int N) { return supported_grid(N); }
 
 cudaError_t run_pass(int N, PassKind kind, const PassArgs& a, int nf, cudaStream_t s) {
+    const int tk = tuned_kind(kind);
+    if (tk >= 0) {
+        const int v = schedule_variant(N, tk);
+        if (v > 0) return run_variant(N, tk, v, a, nf, s);
+    }
     switch (N) {
 #define FFTG_CASE(n) case n: return run_pass_n<n>(kind, a, nf, s);
         FFTG_CASE(3) FFTG_CASE(5) FFTG_CASE(9) FFTG_CASE(15) FFTG_CASE(25) FFTG_CASE(27)
@@ -52,9 +59,12 @@ cudaError_t run_pass(int N, PassKind kind, const PassArgs& a, int nf, cudaStream
     }
 }
 
+// FP32: the most blocks of any schedule variant of the row passes (half the
+// rows per block), so that the partial-sum buffer fits every schedule.
 template <int N>
 static int row_blocks_n(bool fp64) {
-    return fp64 ? Cfg<N, double>::row_blocks : Cfg<N, float>::row_blocks;
+    return fp64 ? Cfg<N, double>::row_blocks
+                : std::max(Cfg<N, float>::row_blocks, Cfg<N, float, Plan<N>::N1, 1>::row_blocks);
 }
 
 int row_blocks(int N, bool fp64) {
@@ -161,7 +171,12 @@ struct fftg_handle {
     double* h_E = nullptr;
     int* h_active = nullptr;
 
-    unsigned int* guard = nullptr;   // loop-pass counter of the CG graph
+    unsigned int* guard = nullptr;   // loop-pass counters: [0] CG graph, [1] Newton loop of a group graph
+    int* run_dev = nullptr;          // device-driven increments (fftg_group_step)
+    double* dE_dev = nullptr;
+    double* Ecom_dev = nullptr;
+    int* fin_dev = nullptr;
+    IncDev* inc_dev = nullptr;
     struct CgGraph {
         int nf = 0;
         const void* tangent = nullptr;
@@ -230,7 +245,8 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 struct Layout {
     size_t off_phase, off_mats, off_eps_star, off_eps_work, off_eps_p, off_eps_p_tr, off_epbar,
         off_epbar_tr, off_sigma, off_tangent, off_x, off_r, off_p, off_q, off_spec, off_tw32,
-        off_tw64, off_twdd, off_partials, off_cg, off_nd, off_E, off_active, off_out36, off_guard, total;
+        off_tw64, off_twdd, off_partials, off_cg, off_nd, off_E, off_active, off_out36, off_guard, off_run,
+        off_dE, off_Ecom, off_fin, off_inc, total;
 };
 
 Layout make_layout(int N, int mixed, int nrhs, int B) {
@@ -276,6 +292,13 @@ Layout make_layout(int N, int mixed, int nrhs, int B) {
     L.off_active = take(Bs * 4);
     L.off_out36 = take(36 * 8);
     L.off_guard = take(64);
+    // device-driven increments (fftg_group_step): per cell run mask, dE,
+    // committed E, finish mask and increment state
+    L.off_run = take(Bs * 4);
+    L.off_dE = take(Bs * 6 * 8);
+    L.off_Ecom = take(Bs * 6 * 8);
+    L.off_fin = take(Bs * 4);
+    L.off_inc = take(Bs * sizeof(IncDev));
     L.total = o;
     return L;
 }
@@ -727,6 +750,30 @@ static void set_cg_params(fftg_handle* h, int nf, double tol, const int* run) {
     }
 }
 
+// eps* += d eps for the cells in the active mask, with ||d eps||^2 per cell
+// (Algorithm 1, iterative update).
+static int launch_newton_update(fftg_handle* h) {
+    VecArgs u{};
+    u.V = h->V;
+    u.cs = h->cs;
+    u.x = h->x;
+    u.eps = h->eps_work;
+    u.nd = h->nd;
+    u.partials = h->partials;
+    u.active = h->active;
+    u.fstride = 6 * h->cs;
+    u.cell_fields = 6 * h->cs;
+    const dim3 g(pointwise_blocks(h->V), h->B);
+    const int slot = prof_begin(h, h->mixed ? KK_NEWTON_UPDATE_F32 : KK_NEWTON_UPDATE_F64);
+    if (h->mixed)
+        k_newton_update<float><<<g, kThreads, 0, h->stream>>>(u);
+    else
+        k_newton_update<double><<<g, kThreads, 0, h->stream>>>(u);
+    prof_end(h, slot);
+    CK(cudaGetLastError());
+    return FFTG_OK;
+}
+
 // ---------------------------------------------------------------- Newton rounds
 namespace fftg_detail {
 
@@ -746,24 +793,8 @@ int newton_round(fftg_handle* h, const int* run, double tol_inner, RoundOut* out
     if (rc) return rc;
     rc = project_solution(h, B, h->active);
     if (rc) return rc;
-    VecArgs u{};
-    u.V = h->V;
-    u.cs = h->cs;
-    u.x = h->x;
-    u.eps = h->eps_work;
-    u.nd = h->nd;
-    u.partials = h->partials;
-    u.active = h->active;
-    u.fstride = 6 * h->cs;
-    u.cell_fields = 6 * h->cs;
-    const dim3 g(pointwise_blocks(h->V), B);
-    const int slot = prof_begin(h, h->mixed ? KK_NEWTON_UPDATE_F32 : KK_NEWTON_UPDATE_F64);
-    if (h->mixed)
-        k_newton_update<float><<<g, kThreads, 0, h->stream>>>(u);
-    else
-        k_newton_update<double><<<g, kThreads, 0, h->stream>>>(u);
-    prof_end(h, slot);
-    CK(cudaGetLastError());
+    rc = launch_newton_update(h);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(h->h_cg, h->cg, B * sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(h->h_nd, h->nd, B * sizeof(NewtonDev), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -960,8 +991,328 @@ static int batch_step(fftg_handle* h, const double* dE, double tol_newton, doubl
     return first;
 }
 
+// ---------------------------------------------------------------- device-driven increments
+// A group of batch handles (cells of several grid sizes) whose increment
+// runs as one CUDA graph launch: per handle, a branch with no dependency on
+// the others, holding
+//   k_inc_begin, eps_work <- eps*,
+//   WHILE (a cell of the handle iterates Newton):           [device test]
+//     k_inc_cg_reset, stress update, residual G sigma, [bounds],
+//     WHILE (a CG solve runs): one CG iteration              [device test]
+//     pending CG step, projection of the inner solution, eps* += d eps,
+//     k_inc_decide (Newton test of Algorithm 1, sets the outer condition)
+//   commit: stress update with history, homogenised stress, trial ->
+//   committed state of the converged cells.
+// The branches of different grid sizes run concurrently on the device.
+struct fftg_group {
+    std::vector<fftg_handle*> hs;
+    std::vector<cudaStream_t> cap;      // two capture streams per handle
+    cudaStream_t stream = nullptr;      // the graph's launch stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double tol_newton = -1.0, tol_cg = -1.0;
+    std::vector<std::vector<IncDev>> h_inc;
+    long long launches = 0;
+};
+
+namespace {
+
+// Adds a WHILE node after the work captured so far on `s` (a stream capturing
+// into some graph) and returns its body; the capture continues after it.
+int add_while(cudaStream_t s, cudaGraphConditionalHandle cond, cudaGraph_t* body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edges, &ndeps) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+        return FFTG_ECUDA;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, edges, ndeps, &p) != cudaSuccess) return FFTG_ECUDA;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return FFTG_ECUDA;
+    *body = p.conditional.phGraph_out[0];
+    return FFTG_OK;
+}
+
+IncArgs inc_args(fftg_handle* h, double tol_newton, double tol_inner) {
+    IncArgs a{};
+    a.B = h->B;
+    a.V = h->V;
+    a.run = h->run_dev;
+    a.dE = h->dE_dev;
+    a.Ecom = h->Ecom_dev;
+    a.Etrial = h->Edev;
+    a.active = h->active;
+    a.fin = h->fin_dev;
+    a.inc = h->inc_dev;
+    a.cg = h->cg;
+    a.nd = h->nd;
+    a.tol_newton = tol_newton;
+    a.max_newton = h->opt.max_newton;
+    a.fixed_newton = h->opt.fixed_newton;
+    a.newton_guard = h->guard + 1;
+    a.cg_guard = h->guard;
+    a.newton_cap = (unsigned int)((h->opt.fixed_newton > 0 ? h->opt.fixed_newton : h->opt.max_newton) + 2);
+    CGState& c = a.cg_template;
+    c.tol2 = tol_inner * tol_inner;
+    c.max_it = h->opt.max_cg;
+    c.fixed_it = h->opt.fixed_cg;
+    c.stag_window = (h->mixed && h->opt.fixed_cg <= 0) ? kStagWindow : 0;
+    return a;
+}
+
+// One handle's branch of the group graph, captured on s1 (into the graph it
+// is capturing) with the Newton body on s2 and the CG body on s3.
+int capture_branch(fftg_handle* h, cudaGraph_t top, cudaStream_t s1, cudaStream_t s2, cudaStream_t s3,
+                   double tol_newton, double tol_cg) {
+    const double tol_inner = h->mixed ? std::max(tol_cg, h->opt.cg_inner_floor) : tol_cg;
+    IncArgs ia = inc_args(h, tol_newton, tol_inner);
+    cudaStream_t own = h->stream;
+    int rc = FFTG_OK;
+    cudaGraphConditionalHandle cN, cC;
+    cudaGraph_t bodyN = nullptr, bodyC = nullptr;
+    h->stream = s1;
+    if (cudaStreamBeginCaptureToGraph(s1, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        h->stream = own;
+        return FFTG_ECUDA;
+    }
+    if (cudaGraphConditionalHandleCreate(&cN, top, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        rc = FFTG_ECUDA;
+    } else {
+        k_inc_begin<<<1, kThreads, 0, s1>>>(cN, ia);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(h->eps_work, h->eps_star, (size_t)h->B * 6 * h->cs * 8, cudaMemcpyDeviceToDevice,
+                            s1) != cudaSuccess)
+            rc = FFTG_ECUDA;
+    }
+    if (rc == FFTG_OK) rc = add_while(s1, cN, &bodyN);
+    // the Newton body
+    if (rc == FFTG_OK) {
+        h->stream = s2;
+        if (cudaStreamBeginCaptureToGraph(s2, bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+            cudaSuccess) {
+            rc = FFTG_ECUDA;
+        } else {
+            if (cudaGraphConditionalHandleCreate(&cC, bodyN, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+                rc = FFTG_ECUDA;
+            } else {
+                k_inc_cg_reset<<<1, kThreads, 0, s2>>>(cC, ia);
+                if (cudaGetLastError() != cudaSuccess) rc = FFTG_ECUDA;
+            }
+            if (rc == FFTG_OK) rc = launch_constitutive(h, h->active, h->B, 0, h->eps_work, h->sigma, false, h->cg);
+            if (rc == FFTG_OK) rc = launch_residual(h);
+            if (rc == FFTG_OK) rc = launch_bounds(h, h->tangent, 7 * h->cs, h->B, 1, h->active);
+            if (rc == FFTG_OK) rc = add_while(s2, cC, &bodyC);
+            // the CG body
+            if (rc == FFTG_OK) {
+                h->stream = s3;
+                if (cudaStreamBeginCaptureToGraph(s3, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+                    cudaSuccess) {
+                    rc = FFTG_ECUDA;
+                } else {
+                    rc = launch_cg_iteration(h, h->B, h->tangent, 7 * h->cs);
+                    const unsigned int cap =
+                        (unsigned int)((h->opt.fixed_cg > 0 ? h->opt.fixed_cg : h->opt.max_cg) + 4);
+                    if (rc == FFTG_OK) {
+                        k_cg_continue<<<1, 32, 0, s3>>>(cC, h->cg, h->B, h->guard, cap);
+                        if (cudaGetLastError() != cudaSuccess) rc = FFTG_ECUDA;
+                    }
+                    cudaGraph_t g3 = nullptr;
+                    if (cudaStreamEndCapture(s3, &g3) != cudaSuccess) rc = FFTG_ECUDA;
+                }
+                h->stream = s2;
+            }
+            if (rc == FFTG_OK) rc = launch_cg_finish(h, h->B);
+            if (rc == FFTG_OK) rc = project_solution(h, h->B, h->active);
+            if (rc == FFTG_OK) rc = launch_newton_update(h);
+            if (rc == FFTG_OK) {
+                k_inc_decide<<<1, kThreads, 0, s2>>>(cN, ia);
+                if (cudaGetLastError() != cudaSuccess) rc = FFTG_ECUDA;
+            }
+            cudaGraph_t g2 = nullptr;
+            if (cudaStreamEndCapture(s2, &g2) != cudaSuccess) rc = FFTG_ECUDA;
+        }
+        h->stream = s1;
+    }
+    // the commit of the converged cells
+    if (rc == FFTG_OK) rc = launch_constitutive(h, h->fin_dev, h->B, 0, h->eps_work, h->sigma, true, nullptr);
+    if (rc == FFTG_OK) {
+        k_inc_end<<<1, kThreads, 0, s1>>>(ia);
+        CommitArgs ca{};
+        ca.fin = h->fin_dev;
+        ca.eps_star = h->eps_star;
+        ca.eps_work = h->eps_work;
+        ca.eps_p = h->eps_p;
+        ca.eps_p_tr = h->eps_p_tr;
+        ca.epbar = h->epbar;
+        ca.epbar_tr = h->epbar_tr;
+        ca.cs = h->cs;
+        k_inc_commit<<<dim3(vector_blocks(6 * h->cs, 8), h->B), kThreads, 0, s1>>>(ca);
+        if (cudaGetLastError() != cudaSuccess) rc = FFTG_ECUDA;
+    }
+    cudaGraph_t g1 = nullptr;
+    if (cudaStreamEndCapture(s1, &g1) != cudaSuccess) rc = FFTG_ECUDA;
+    h->stream = own;
+    return rc;
+}
+
+void group_free_graph(fftg_group* g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->exec = nullptr;
+    g->graph = nullptr;
+}
+
+int group_build(fftg_group* g, double tol_newton, double tol_cg) {
+    group_free_graph(g);
+    if (cudaGraphCreate(&g->graph, 0) != cudaSuccess) return FFTG_ECUDA;
+    int rc = FFTG_OK;
+    for (size_t k = 0; k < g->hs.size() && rc == FFTG_OK; ++k) {
+        fftg_handle* h = g->hs[k];
+        const long long before = h->launches;
+        const bool prof_on = h->prof && h->prof->on;
+        if (prof_on) h->prof->on = false;  // no per-launch events inside the graph
+        rc = capture_branch(h, g->graph, g->cap[3 * k], g->cap[3 * k + 1], g->cap[3 * k + 2], tol_newton, tol_cg);
+        if (prof_on) h->prof->on = true;
+        h->launches = before;  // capture enqueues nothing
+    }
+    if (rc == FFTG_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = FFTG_ECUDA;
+    if (rc != FFTG_OK) {
+        cudaGetLastError();
+        group_free_graph(g);
+        return rc;
+    }
+    g->tol_newton = tol_newton;
+    g->tol_cg = tol_cg;
+    return FFTG_OK;
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------- public API
 extern "C" {
+
+int fftg_group_create(fftg_group** out, fftg_handle* const* handles, int n) {
+    if (!out || !handles || n < 1) return FFTG_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!handles[k] || handles[k]->opt.solver != FFTG_SOLVER_CG) return FFTG_EINVAL;
+        for (int j = 0; j < k; ++j)
+            if (handles[j] == handles[k]) return FFTG_EINVAL;
+    }
+    fftg_group* g = new (std::nothrow) fftg_group();
+    if (!g) return FFTG_ENOMEM;
+    g->hs.assign(handles, handles + n);
+    g->h_inc.resize(n);
+    bool ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess;
+    g->cap.assign(3 * n, nullptr);
+    for (int k = 0; k < 3 * n && ok; ++k) ok = cudaStreamCreateWithFlags(&g->cap[k], cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < n; ++k) g->h_inc[k].resize(handles[k]->B);
+    if (!ok) {
+        cudaGetLastError();
+        fftg_group_destroy(g);
+        return FFTG_ECUDA;
+    }
+    *out = g;
+    return FFTG_OK;
+}
+
+void fftg_group_destroy(fftg_group* g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    group_free_graph(g);
+    for (cudaStream_t s : g->cap)
+        if (s) cudaStreamDestroy(s);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+int fftg_group_step(fftg_group* g, const double* dE, const int* run, double tol_newton, double tol_cg,
+                    double* sigma_out, int* newton_iters, int* cg_iters, int* status) {
+    if (!g || !dE || !sigma_out || !status || !(tol_newton > 0) || !(tol_cg > 0)) return FFTG_EINVAL;
+    size_t total = 0;
+    for (fftg_handle* h : g->hs) total += (size_t)h->B;
+    for (size_t i = 0; i < 6 * total; ++i)
+        if (!std::isfinite(dE[i])) return FFTG_ENAN;
+    for (fftg_handle* h : g->hs)
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return FFTG_ECUDA;
+    if (!g->exec || g->tol_newton != tol_newton || g->tol_cg != tol_cg) {
+        const int rc = group_build(g, tol_newton, tol_cg);
+        if (rc) return rc;
+    }
+    // inputs: per handle the run mask, dE and the committed E
+    std::vector<int> runs(total, 1);
+    if (run)
+        for (size_t i = 0; i < total; ++i) runs[i] = run[i] ? 1 : 0;
+    size_t off = 0;
+    for (fftg_handle* h : g->hs) {
+        const int B = h->B;
+        if (cudaMemcpyAsync(h->run_dev, runs.data() + off, B * sizeof(int), cudaMemcpyHostToDevice, g->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(h->dE_dev, dE + 6 * off, (size_t)B * 48, cudaMemcpyHostToDevice, g->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(h->Ecom_dev, h->E.data(), (size_t)B * 48, cudaMemcpyHostToDevice, g->stream) !=
+                cudaSuccess)
+            return FFTG_ECUDA;
+        off += (size_t)B;
+    }
+    if (cudaGraphLaunch(g->exec, g->stream) != cudaSuccess) return FFTG_ECUDA;
+    for (size_t k = 0; k < g->hs.size(); ++k) {
+        fftg_handle* h = g->hs[k];
+        if (cudaMemcpyAsync(g->h_inc[k].data(), h->inc_dev, (size_t)h->B * sizeof(IncDev),
+                            cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+            return FFTG_ECUDA;
+    }
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return FFTG_ECUDA;
+    int first = FFTG_OK;
+    off = 0;
+    for (size_t k = 0; k < g->hs.size(); ++k) {
+        fftg_handle* h = g->hs[k];
+        int max_newton = 0, max_cg = 0;
+        for (int b = 0; b < h->B; ++b, ++off) {
+            const IncDev& s = g->h_inc[k][b];
+            const bool on = runs[off] != 0;
+            reset_stats(h, b);
+            fftg_stats& st = h->stats[b];
+            st.newton_iters = s.newton;
+            st.cg_iters = s.cg;
+            st.status = on ? (s.state == INC_DONE ? FFTG_OK : s.state == INC_FAILED ? s.status : FFTG_ENOCONV_NEWTON)
+                           : FFTG_OK;
+            status[off] = st.status;
+            if (newton_iters) newton_iters[off] = s.newton;
+            if (cg_iters) cg_iters[off] = s.cg;
+            if (on && s.state == INC_DONE) {
+                for (int c = 0; c < 6; ++c) {
+                    sigma_out[6 * off + c] = s.sigma[c];
+                    h->E[6 * b + c] += dE[6 * off + c];
+                }
+                h->have_tangent[b] = 1;
+                h->have_update[b] = 1;
+            }
+            if (on && st.status != FFTG_OK && first == FFTG_OK) first = st.status;
+            max_newton = std::max(max_newton, s.newton);
+            max_cg = std::max(max_cg, s.cg);
+        }
+        // kernels of the branch: begin, end, commit, the commit's stress
+        // update; per Newton pass 15 outside the CG loop; per CG loop pass
+        // the iteration's kernels and the loop test (an upper bound when
+        // the cells' CG counts differ between Newton passes)
+        const long long per_cg = cg_fused(h) ? 6 : 7;
+        h->launches += 4 + 15LL * max_newton + (per_cg + 1) * (max_cg + max_newton);
+        g->launches += 4 + 15LL * max_newton + (per_cg + 1) * (max_cg + max_newton);
+    }
+    return first;
+}
+
+long long fftg_group_launch_count(const fftg_group* g) { return g ? g->launches : 0; }
+
 
 void fftg_default_options(fftg_options* o) {
     if (!o) return;
@@ -1066,6 +1417,11 @@ int fftg_create_batch(fftg_handle** out, int N, int ncells, const uint8_t* phase
     h->active = (int*)(h->ws + L.off_active);
     h->out36 = (double*)(h->ws + L.off_out36);
     h->guard = (unsigned int*)(h->ws + L.off_guard);
+    h->run_dev = (int*)(h->ws + L.off_run);
+    h->dE_dev = (double*)(h->ws + L.off_dE);
+    h->Ecom_dev = (double*)(h->ws + L.off_Ecom);
+    h->fin_dev = (int*)(h->ws + L.off_fin);
+    h->inc_dev = (IncDev*)(h->ws + L.off_inc);
 
     auto fail = [&](int code) {
         fftg_destroy(h);

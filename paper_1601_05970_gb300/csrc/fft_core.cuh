@@ -235,21 +235,34 @@ FFTG_PLAN(225, 15, 15)
 FFTG_PLAN(243, 27, 9)
 #undef FFTG_PLAN
 
+// Radix schedules other than the default split N = N1 * N2 (the kernels
+// take N1 as a template parameter; N2 = N / N1). A schedule is valid when
+// N1 divides N and both factors are products of 3 and 5.
+constexpr bool radix35(int n) {
+    while (n % 3 == 0) n /= 3;
+    while (n % 5 == 0) n /= 5;
+    return n == 1;
+}
+constexpr bool valid_split(int N, int N1) { return N1 >= 1 && N % N1 == 0 && radix35(N1) && radix35(N / N1); }
+
 // position of frequency k after a forward stage B in permuted mode
-template <int N>
+template <int N, int N1 = Plan<N>::N1>
 __device__ __forceinline__ int perm_pos(int k) {
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N2 = N / N1;
     return N2 * (k % N1) + k / N1;
 }
 
 // ---------------------------------------------------------------- stages
 // src/dst: pencil base pointers; ss/ds: element strides (in cplx units).
+// Each stage exists for the default split (Plan<N>) and, with the first
+// factor N1 given explicitly, for any valid split.
 
 // forward stage A: reads positions t + N2*m, writes t + N2*k1 (with twiddle)
-template <int N, typename T>
+template <int N, int N1, typename T>
 __device__ __forceinline__ void fwdA(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int t,
                                      const cplx<T>* __restrict__ tw) {
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    static_assert(valid_split(N, N1), "radix schedule");
+    constexpr int N2 = N / N1;
     cplx<T> v[N1];
 #pragma unroll
     for (int m = 0; m < N1; ++m) v[m] = src[(t + N2 * m) * ss];
@@ -263,10 +276,10 @@ __device__ __forceinline__ void fwdA(const cplx<T>* src, int ss, cplx<T>* dst, i
 }
 
 // forward stage B: reads N2*k1 + q; NATURAL: writes k1 + N1*k2, else N2*k1 + k2
-template <int N, bool NATURAL, typename T>
+template <int N, int N1, bool NATURAL, typename T>
 __device__ __forceinline__ void fwdB(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int k1,
                                      const cplx<T>* __restrict__ tw) {
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N2 = N / N1;
     cplx<T> v[N2];
 #pragma unroll
     for (int q = 0; q < N2; ++q) v[q] = src[(N2 * k1 + q) * ss];
@@ -277,10 +290,10 @@ __device__ __forceinline__ void fwdB(const cplx<T>* src, int ss, cplx<T>* dst, i
 
 // inverse stage B': NATURAL: reads k1 + N1*k2, else N2*k1 + k2;
 // writes N2*k1 + t with the conjugate twiddle
-template <int N, bool NATURAL, typename T>
+template <int N, int N1, bool NATURAL, typename T>
 __device__ __forceinline__ void invB(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int k1,
                                      const cplx<T>* __restrict__ tw) {
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N2 = N / N1;
     cplx<T> v[N2];
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) v[k2] = src[(NATURAL ? (k1 + N1 * k2) : (N2 * k1 + k2)) * ss];
@@ -294,16 +307,38 @@ __device__ __forceinline__ void invB(const cplx<T>* src, int ss, cplx<T>* dst, i
 }
 
 // inverse stage A': reads t + N2*k1, writes t + N2*m
-template <int N, typename T>
+template <int N, int N1, typename T>
 __device__ __forceinline__ void invA(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int t,
                                      const cplx<T>* __restrict__ tw) {
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N2 = N / N1;
     cplx<T> v[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(t + N2 * k1) * ss];
     RegDFT<N, N1, +1, T>::run(v, tw);
 #pragma unroll
     for (int m = 0; m < N1; ++m) dst[(t + N2 * m) * ds] = v[m];
+}
+
+// the stages with the default split
+template <int N, typename T>
+__device__ __forceinline__ void fwdA(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int t,
+                                     const cplx<T>* __restrict__ tw) {
+    fwdA<N, Plan<N>::N1, T>(src, ss, dst, ds, t, tw);
+}
+template <int N, bool NATURAL, typename T>
+__device__ __forceinline__ void fwdB(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int k1,
+                                     const cplx<T>* __restrict__ tw) {
+    fwdB<N, Plan<N>::N1, NATURAL, T>(src, ss, dst, ds, k1, tw);
+}
+template <int N, bool NATURAL, typename T>
+__device__ __forceinline__ void invB(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int k1,
+                                     const cplx<T>* __restrict__ tw) {
+    invB<N, Plan<N>::N1, NATURAL, T>(src, ss, dst, ds, k1, tw);
+}
+template <int N, typename T>
+__device__ __forceinline__ void invA(const cplx<T>* src, int ss, cplx<T>* dst, int ds, int t,
+                                     const cplx<T>* __restrict__ tw) {
+    invA<N, Plan<N>::N1, T>(src, ss, dst, ds, t, tw);
 }
 
 }  // namespace fftg

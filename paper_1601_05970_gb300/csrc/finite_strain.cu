@@ -333,7 +333,7 @@ const char* const kFsKindNames[FSK_COUNT] = {
     "fs_p5_plain_f64", "fs_p5_plain_f32", "fs_p5_dot_f64", "fs_p5_dot_f32",
     "fs_p5_rhs_f64_to_f64", "fs_p5_rhs_f64_to_f32", "fs_p1_plain_dd", "fs_p2_dd", "fs_p3_dd", "fs_p4_dd",
     "fs_p5_rhs_dd_to_f32", "fs_p5_plain_dd_to_f64", "fs_p1_tanrhs_f64", "fs_p1_tanrhs_f32",
-    "fs_p5_rhs_f32_to_f32",
+    "fs_p5_rhs_f32_to_f32", "fs_p1_cgf_f32", "fs_p5_cgf_f32",
     "fs_constitutive_f32", "fs_constitutive_f64", "fs_cg_update_f32", "fs_cg_update_f64",
     "fs_cg_finish_f32", "fs_cg_finish_f64", "fs_newton_update_f32", "fs_newton_update_f64",
     "fs_tangent_floor", "fs_tangent_average"};
@@ -577,12 +577,38 @@ int fs_residual(fftg_fs_handle* h) {
     return FFTG_OK;
 }
 
+// The mixed path's CG runs without the update pass: alpha from <p, K : p>
+// in P1, r -= alpha q in P5 (fs_passes.cuh, FS_P1_CGF). 0: P1 / P5 with
+// <p, q> and the update pass, as in the FP64 path.
+#ifndef FFTG_FS_CG_FUSED
+#define FFTG_FS_CG_FUSED 1
+#endif
+bool fs_cg_fused(const fftg_fs_handle* h) { return FFTG_FS_CG_FUSED && h->mixed; }
+
 // One CG iteration: P1 (x, p updates and K : p), P2-P4, P5 (q, <p, q>),
-// then r -= alpha q.
+// then r -= alpha q; in the mixed path P1 (with <p, K : p>), P2-P4 and P5
+// (r -= alpha q, <r, r>).
 int fs_cg_iteration(fftg_fs_handle* h) {
     const bool f64 = !h->mixed;
     const double invN3 = 1.0 / ((double)h->N * h->N * h->N);
     const int prec = f64 ? FFT_F64 : FFT_F32;
+    if (fs_cg_fused(h)) {
+        FsArgs a = fs_args(h, FFT_F32);
+        a.aux = h->r;
+        a.aux2 = h->p;
+        a.aux3 = h->x;
+        a.cg = h->cg;
+        CK(fs_pass(h, FK_P1_CGF_F32, a));
+        int rc = fs_p234(h, FFT_F32, invN3, h->cg);
+        if (rc) return rc;
+        FsArgs b = fs_args(h, FFT_F32);
+        b.in = h->spec;
+        b.aux = h->r;
+        b.aux3 = h->r;
+        b.cg = h->cg;
+        CK(fs_pass(h, FK_P5_CGF_F32, b));
+        return FFTG_OK;
+    }
     FsArgs a = fs_args(h, prec);
     a.aux = h->r;
     a.aux2 = h->p;
@@ -682,7 +708,7 @@ int fs_run_cg(fftg_fs_handle* h) {
             if (rc) return rc;
             CK(cudaMemcpyAsync(h->h_cg, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
-            h->launches += 7LL * (h->h_cg->it + 1);  // one of each per loop pass
+            h->launches += (fs_cg_fused(h) ? 6LL : 7LL) * (h->h_cg->it + 1);  // one of each per loop pass
             return FFTG_OK;
         }
     }

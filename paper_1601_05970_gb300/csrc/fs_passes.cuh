@@ -28,8 +28,12 @@ namespace fftg {
 constexpr int kFsComp = 9;
 constexpr int kFsPairs = 5;
 
-enum : int { FS_P1_PLAIN = 0, FS_P1_TAN = 1, FS_P1_CG = 2, FS_P1_TANRHS = 3 };
-enum : int { FS_P5_PLAIN = 0, FS_P5_DOT = 1, FS_P5_RHS = 2 };
+enum : int { FS_P1_PLAIN = 0, FS_P1_TAN = 1, FS_P1_CG = 2, FS_P1_TANRHS = 3, FS_P1_CGF = 4 };
+enum : int { FS_P5_PLAIN = 0, FS_P5_DOT = 1, FS_P5_RHS = 2, FS_P5_CGF = 3 };
+// FS_P1_CGF / FS_P5_CGF: the CG iteration without the update pass, as in
+// the small-strain passes (P1_CGF): G projects orthogonally onto gradient
+// fields, so <p, G K p> = <p, K p> for a gradient field p; P1 reduces
+// <p, K : p> (alpha), P5 updates r -= alpha q and reduces <r, r>.
 
 struct FsArgs {
     const void* in;        // P1: real field; P5: spectrum
@@ -160,7 +164,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* z = tw + N;  // [5][R][N]
-    if (MODE == FS_P1_CG && a.cg->done) return;
+    constexpr bool CGM = MODE == FS_P1_CG || MODE == FS_P1_CGF;
+    if (CGM && a.cg->done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
     const int row0 = blockIdx.x * R;
@@ -169,8 +174,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
     const int nel = nrows * N;
     const long long cs = a.cs;
     T beta = T(0), alpha = T(0);
+    T pkp = T(0);  // FS_P1_CGF: this thread's part of <p, K : p>
     bool first = true;
-    if (MODE == FS_P1_CG) {
+    if (CGM) {
         beta = (T)a.cg->beta;
         alpha = (T)a.cg->alpha;
         first = a.cg->it == 0;
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
             const long long v0 = base + i0;
             T p[9][VW], h[9][VW];
             int ph[VW];
-            if (MODE == FS_P1_CG) {
+            if (CGM) {
                 const T* r = (const T*)a.aux;
                 T* pp = (T*)a.aux2;
                 T* xx = (T*)a.aux3;
@@ -260,6 +266,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
                     svk_tangent_apply<T>(he, (T)m[0], (T)m[1], pe, se);
 #pragma unroll
                     for (int c = 0; c < 9; ++c) s[c][e] = se[c];
+                    if (MODE == FS_P1_CGF && i0 + e < nel) {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) pkp += pe[c] * se[c];
+                    }
                 }
             }
         } else {
@@ -307,6 +317,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
                 out[(2 * c + 1) * HS + o] = mk(T(0.5) * d.y, T(-0.5) * d.x);
             }
         }
+    }
+    if (MODE == FS_P1_CGF) {
+        // alpha = <r, r> / <p, K : p>
+        CGState* cg = a.cg;
+        const int nb = gridDim.x;
+        double part[1] = {block_sum((double)pkp)};
+        if (!publish_partials<1>(part, a.partials, blockIdx.x, nb, &cg->ticket)) return;
+        double tot[1];
+        reduce_partials<1>(a.partials, nb, &cg->ticket, tot);
+        if (tid == 0) cg_after_dot(cg, tot[0]);
     }
 }
 
@@ -399,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* z = tw + N;  // [5][R][N]
     CGState* cg = a.cg;
-    if (MODE == FS_P5_DOT && cg->done) return;
+    if ((MODE == FS_P5_DOT || MODE == FS_P5_CGF) && cg->done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
     const int row0 = blockIdx.x * R;
@@ -460,7 +480,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
     __syncthreads();
     const long long cs = a.cs;
     TO* out = (TO*)a.out;
-    const TO* pin = (const TO*)a.aux;
+    const TO* pin = (const TO*)a.aux;   // FS_P5_DOT: p; FS_P5_CGF: r
+    TO* rout = MODE == FS_P5_CGF ? (TO*)a.aux3 : nullptr;
+    const TO alpha = MODE == FS_P5_CGF ? (TO)cg->alpha : TO(0);
     T acc0 = T(0);
     double acc1 = 0.0;
     // VO voxels per lane (at most 16 bytes of TO): p is loaded before q is
@@ -472,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
         if (i0 >= nel) continue;
         const long long v0 = base + i0;
         TO pv[9][VO];
-        if (MODE == FS_P5_DOT) {
+        if (MODE == FS_P5_DOT || MODE == FS_P5_CGF) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) ldv<VO, TO>(pin + c * cs + v0, pv[c]);
         }
@@ -489,6 +511,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
             qd[8][e] = z[4 * R * N + i0 + e].x;
 #pragma unroll
             for (int c = 0; c < 9; ++c) q[c][e] = (TO)qd[c][e];
+        }
+        if (MODE == FS_P5_CGF) {
+            // r -= alpha q, <r, r> (lanes past the grid update padding only)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+#pragma unroll
+                for (int e = 0; e < VO; ++e) pv[c][e] -= alpha * q[c][e];
+                stv<VO, TO>(rout + c * cs + v0, pv[c]);
+            }
+#pragma unroll
+            for (int e = 0; e < VO; ++e) {
+                if (i0 + e >= nel) continue;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) acc0 += (T)(pv[c][e] * pv[c][e]);
+            }
+            continue;
         }
 #pragma unroll
         for (int c = 0; c < 9; ++c) stv<VO, TO>(out + c * cs + v0, q[c]);
@@ -518,6 +556,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
     if (tid != 0) return;
     if (MODE == FS_P5_DOT)
         cg_after_dot(cg, tot[0]);
+    else if (MODE == FS_P5_CGF)
+        cg_after_update(cg, tot[0]);
     else
         cg_start(cg, tot[0], tot[1]);
 }
@@ -532,6 +572,8 @@ enum FsPassKind : int {
     FK_P1_PLAIN_DD, FK_P2_DD, FK_P3_DD, FK_P4_DD, FK_P5_RHS_DD_TO_F32, FK_P5_PLAIN_DD_TO_F64,
     // right-hand sides of the macroscopic tangent
     FK_P1_TANRHS_F64, FK_P1_TANRHS_F32, FK_P5_RHS_F32_TO_F32,
+    // the CG iteration without the update pass (FS_P1_CGF / FS_P5_CGF), FP32
+    FK_P1_CGF_F32, FK_P5_CGF_F32,
     FK_COUNT
 };
 
@@ -609,6 +651,8 @@ cudaError_t run_fs_pass_n(FsPassKind kind, const FsArgs& a, cudaStream_t s) {
         case FK_P1_TANRHS_F32: return launch_fs(k_fs_p1<N, float, FS_P1_TANRHS>, r32, kThreads, m32, a, s);
         case FK_P5_RHS_F32_TO_F32:
             return launch_fs(k_fs_p5<N, float, FS_P5_RHS, float>, r32, kThreads, m32, a, s);
+        case FK_P1_CGF_F32: return launch_fs(k_fs_p1<N, float, FS_P1_CGF>, r32, kThreads, m32, a, s);
+        case FK_P5_CGF_F32: return launch_fs(k_fs_p5<N, float, FS_P5_CGF, float>, r32, kThreads, m32, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

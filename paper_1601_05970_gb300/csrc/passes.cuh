@@ -22,15 +22,32 @@
 
 namespace fftg {
 
-enum : int { P1_PLAIN = 0, P1_TAN = 1, P1_CG = 2, P1_TANRHS = 3 };
-enum : int { P5_PLAIN = 0, P5_DOT = 1, P5_RHS = 2 };
+enum : int { P1_PLAIN = 0, P1_TAN = 1, P1_CG = 2, P1_TANRHS = 3, P1_CGF = 4 };
+enum : int { P5_PLAIN = 0, P5_DOT = 1, P5_RHS = 2, P5_CGF = 3 };
+
+// The two CG iterations of the passes.
+//
+// P1_CG / P5_DOT (+ the update kernel): Hestenes-Stiefel CG on G C as
+// written, alpha = <r, r> / <p, G C p> from the product of P5, then
+// r -= alpha q and <r, r> in a separate pass over r and q.
+//
+// P1_CGF / P5_CGF (mixed path): on compatible fields G is the orthogonal
+// projector onto them, so <p, G C p> = <G p, C p> = <p, C p>; P1 forms
+// C : p anyway and reduces <p, C : p> there, so alpha is known before P5,
+// which then updates r -= alpha q with q still in registers and reduces
+// <r, r>: q is never stored and the update pass disappears (72 B per voxel
+// and field less per iteration in FP32). The iterates are those of CG up to
+// the rounding of the incompatible part that the FP32 recursion leaves in p
+// (about 1e-5 of |p| after some tens of iterations, removed by the
+// projection of each inner solution).
 
 struct PassArgs {
     const void* in;        // P1: real field; P2-P4: unused; P5: spectrum
     void* out;             // P1: spectrum; P2-P4: spectrum (in place); P5: real field
     const void* aux;       // P1_CG: r; P5_DOT: p
     void* aux2;            // P1_CG: p (updated in place)
-    void* aux3;            // P1_CG: x (gets the previous iteration's alpha p)
+    void* aux3;            // P1_CG: x (gets the previous iteration's alpha p);
+                           // P5_CGF: r (updated in place; aux is the same r)
     const void* tangent;   // [7][V]: K', 2G_eff, w11, w22, w23, w13, w12 (see apply_tangent7)
     CGState* cg;           // per field, or null
     double* partials;      // [nf][nblocks][2]
@@ -147,19 +164,28 @@ __device__ __forceinline__ void stv(T* p, const T (&v)[W]) {
     *reinterpret_cast<VT*>(p) = t;
 }
 
-template <int N, typename T>
+// Block shapes of the passes for the radix split N = NA * (N / NA) and the
+// tile variant TV (the autotuner's schedules; NA = Plan<N>::N1, TV = 0 are
+// the defaults): P1/P5 rows per block R (TV 1: half, 2: double), P3
+// columns per block W3 (TV 1: half, 2: double, within the shared memory of
+// a block), P2/P4 columns per block W2 (FP32, TV 1: 32 instead of 16).
+template <int N, typename T, int NA = Plan<N>::N1, int TV = 0>
 struct Cfg {
+    static constexpr int PN1 = NA, PN2 = N / NA;
     static constexpr int H = (N + 1) / 2;
     static constexpr int CS = (int)sizeof(cplx<T>);
     static constexpr int BUDGET = 100 * 1024;
     static constexpr int ROW_BUDGET = 50 * 1024;
+    static constexpr int SMEM_MAX = 227 * 1024;
     static constexpr int fl2(int x) {
         return x >= 64 ? 64 : x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1;
     }
     // rows per block in P1/P5: a power of two >= 4, so that a block's rows
     // are a whole number of 16-byte vectors
     static constexpr int R0 = FFTG_ROWS > 0 ? FFTG_ROWS : fl2(ROW_BUDGET / (3 * N * CS));
-    static constexpr int R = R0 < 4 ? 4 : R0;
+    static constexpr int R1 = R0 < 4 ? 4 : R0;
+    static constexpr int R = TV == 1 ? (R1 / 2 < 4 ? 4 : R1 / 2)
+                             : TV == 2 && (size_t)(3 * 2 * R1 * N + N) * CS <= SMEM_MAX ? 2 * R1 : R1;
     // voxels per lane in P1's elementwise phase (FP64: at most 2 = 16 bytes)
     static constexpr int VW = (sizeof(T) == 8 && FFTG_P1_VW > 2) ? 2 : FFTG_P1_VW;
     static constexpr int W3a = fl2(BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(BUDGET / (6 * N * CS));
@@ -168,25 +194,31 @@ struct Cfg {
     // took the pass from 3.35 to 2.29 ms against 4 (the FP64 rule); 2
     // columns 3.33 ms
     static constexpr int WDa = fl2(2 * BUDGET / (6 * N * CS)) > 32 ? 32 : fl2(2 * BUDGET / (6 * N * CS));
-    static constexpr int WDt = Plan<N>::N2 == 1 ? 32
-                               : (fl2(512 / (6 * Plan<N>::N2)) < fl2(512 / (2 * Plan<N>::N1))
-                                      ? fl2(512 / (6 * Plan<N>::N2))
-                                      : fl2(512 / (2 * Plan<N>::N1)));
+    static constexpr int WDt = PN2 == 1 ? 32
+                               : (fl2(512 / (6 * PN2)) < fl2(512 / (2 * PN1))
+                                      ? fl2(512 / (6 * PN2))
+                                      : fl2(512 / (2 * PN1)));
     static constexpr int WD = WDa < WDt ? WDa : WDt;
-    static constexpr int W3 = is_dd_v<T> ? (FFTG_DD_P3_W > 0 ? FFTG_DD_P3_W : (WD > W3a ? WD : W3a))
-                              : (FFTG_P3_W > 0 && FFTG_P3_W < W3a) ? FFTG_P3_W : W3a;
-    static constexpr int W2 = (CS == 8) ? 32 : 16;                            // columns, P2/P4
-    static constexpr int S2 = fl2(BUDGET / (N * W2 * CS)) > 16 ? 16 : fl2(BUDGET / (N * W2 * CS));
+    static constexpr int W3d = is_dd_v<T> ? (FFTG_DD_P3_W > 0 ? FFTG_DD_P3_W : (WD > W3a ? WD : W3a))
+                               : (FFTG_P3_W > 0 && FFTG_P3_W < W3a) ? FFTG_P3_W : W3a;
     static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
     static constexpr int cap(int x) { return x > 1024 ? 1024 : x; }
+    static constexpr bool p3_fits(int w) {
+        return (size_t)(6 * w * N + N) * CS <= SMEM_MAX && rup32(6 * w * PN2) <= 1024 &&
+               rup32(2 * w * PN1) <= 1024;
+    }
+    static constexpr int W3 = TV == 1 ? (W3d / 2 < 1 ? 1 : W3d / 2)
+                              : TV == 2 && W3d < 32 && p3_fits(2 * W3d) ? 2 * W3d : W3d;
+    static constexpr int W2 = (CS == 8) ? (TV == 1 ? 32 : 16) : 32;         // columns, P2/P4
+    static constexpr int S2 = fl2(BUDGET / (N * W2 * CS)) > 16 ? 16 : fl2(BUDGET / (N * W2 * CS));
     // threads of the column passes: one stage-A item per thread
-    static constexpr int T2 = cap(rup32(S2 * W2 * Plan<N>::N2));
+    static constexpr int T2 = cap(rup32(S2 * W2 * PN2));
     // P3: one stage-A item per thread, and (FFTG_P3_TB) at least 2*W*N1
     // threads (448 at 243^3 rather than 432: the configuration measured)
-    static constexpr int T3a = rup32(6 * W3 * Plan<N>::N2);
-    static constexpr int T3b = FFTG_P3_TB ? rup32(2 * W3 * Plan<N>::N1) : 0;
+    static constexpr int T3a = rup32(6 * W3 * PN2);
+    static constexpr int T3b = FFTG_P3_TB ? rup32(2 * W3 * PN1) : 0;
     // single-stage plans (N2 = 1) loop over the middle stages with 256 threads
-    static constexpr int T3 = Plan<N>::N2 == 1 ? (T3a > 256 ? cap(T3a) : 256) : cap(T3a > T3b ? T3a : T3b);
+    static constexpr int T3 = PN2 == 1 ? (T3a > 256 ? cap(T3a) : 256) : cap(T3a > T3b ? T3a : T3b);
     static constexpr size_t smem_rows = (size_t)(3 * R * N + N) * CS;
     static constexpr size_t smem_p3 = (size_t)(6 * W3 * N + N) * CS;
     static constexpr size_t smem_p24 = (size_t)(S2 * W2 * N + N) * CS;
@@ -246,18 +278,19 @@ struct Vec16<double> {
 };
 
 // ----------------------------------------------------------------------- P1
-template <int N, typename T, int MODE>
+template <int N, typename T, int MODE, int NA = Plan<N>::N1, int TV = 0>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_dd_v<T> ? FFTG_DD_MINB : 2)
     k_p1(PassArgs a) {
-    using C = Cfg<N, T>;
+    using C = Cfg<N, T, NA, TV>;
     constexpr int R = C::R, H = C::H;
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N1 = NA, N2 = N / NA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* z = tw + N;  // [3][R][N]
     const int f = blockIdx.z;
     if (a.active && !a.active[f]) return;
-    if (MODE == P1_CG && a.cg[f].done) return;
+    constexpr bool CGM = MODE == P1_CG || MODE == P1_CGF;
+    if (CGM && a.cg[f].done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
     const int row0 = blockIdx.x * R;
@@ -269,8 +302,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
     const TIn* in = (const TIn*)a.in + f * a.fstride;
     const T* tg = (const T*)a.tangent + f * a.tstride;
     T beta = T(0), alpha = T(0);
+    T pcp = T(0);       // P1_CGF: this thread's part of <p, C : p>
     bool first = true;  // first CG iteration: p = r (p holds no data yet)
-    if (MODE == P1_CG) {
+    if (CGM) {
         beta = (T)a.cg[f].beta;
         alpha = (T)a.cg[f].alpha;
         first = a.cg[f].it == 0;
@@ -289,9 +323,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
         if (i0 < nel) {
             const long long v0 = base + i0;
             T p[6][VW];
-            if (MODE == P1_CG) {
+            if (CGM) {
                 // x += alpha p (the step of the previous iteration, which the
-                // update kernel left to this pass), then p = r + beta p
+                // update left to this pass), then p = r + beta p
                 const T* r = (const T*)a.aux + f * a.fstride;
                 T* pp = (T*)a.aux2 + f * a.fstride;
                 T* xx = (T*)a.aux3 + f * a.fstride;
@@ -342,6 +376,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
                                       t7[6][e], pe, se);
 #pragma unroll
                     for (int c = 0; c < 6; ++c) s[c][e] = se[c];
+                    if (MODE == P1_CGF && i0 + e < nel) pcp += frob<T>(pe, se);
                 }
             }
         } else {
@@ -361,13 +396,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
     constexpr int NP = 3 * R;
     for (int it = tid; it < NP * N2; it += kThreads) {
         const int pc = it % NP, t = it / NP;
-        if (pc % R < nrows) fwdA<N, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
+        if (pc % R < nrows) fwdA<N, N1, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
     }
     __syncthreads();
     if (N2 > 1) {
         for (int it = tid; it < NP * N1; it += kThreads) {
             const int pc = it % NP, k1 = it / NP;
-            if (pc % R < nrows) fwdB<N, false, T>(z + pc * N, 1, z + pc * N, 1, k1, tw);
+            if (pc % R < nrows) fwdB<N, N1, false, T>(z + pc * N, 1, z + pc * N, 1, k1, tw);
         }
         __syncthreads();
     }
@@ -375,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
     const long long HS = (long long)N * N * H;
     for (int it = tid; it < nrows * H; it += kThreads) {
         const int row = it / H, k = it - row * H;
-        const int pk = perm_pos<N>(k), pn = perm_pos<N>(k == 0 ? 0 : N - k);
+        const int pk = perm_pos<N, N1>(k), pn = perm_pos<N, N1>(k == 0 ? 0 : N - k);
         const long long o = (long long)(row0 + row) * H + k;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -388,17 +423,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
             out[(2 * c + 1) * HS + o] = B;
         }
     }
+    if (MODE == P1_CGF) {
+        // alpha = <r, r> / <p, C : p> (see P1_CGF above)
+        CGState* cg = a.cg + f;
+        const int nb = gridDim.x;
+        double part[1] = {block_sum((double)pcp)};
+        double* partials = a.partials + (size_t)f * nb;
+        if (!publish_partials<1>(part, partials, blockIdx.x, nb, &cg->ticket)) return;
+        double tot[1];
+        reduce_partials<1>(partials, nb, &cg->ticket, tot);
+        if (tid == 0) cg_after_dot(cg, tot[0]);
+    }
 }
 
 // -------------------------------------------------------------- P2 / P4 (x2)
 // Blocks of T2 = (slabs x columns x N2) threads: stage A is one item per
 // thread; stage B takes N1/N2 rounds. A slab is one (component, x1) plane
 // of the spectrum; NC components (6 here, 9 in the finite-strain passes).
-template <int N, typename T, bool FWD, int NC = 6>
-__global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
-    using C = Cfg<N, T>;
+template <int N, typename T, bool FWD, int NC = 6, int NA = Plan<N>::N1, int TV = 0>
+__global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T2) k_p24(PassArgs a) {
+    using C = Cfg<N, T, NA, TV>;
     constexpr int H = C::H, W = C::W2, S = C::S2, NT = C::T2;
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N1 = NA, N2 = N / NA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf = tw + N;  // [S][N][W]
@@ -416,28 +462,28 @@ __global__ void __launch_bounds__(Cfg<N, T>::T2) k_p24(PassArgs a) {
             const int pc = it % P, t = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < NC * N)
-                fwdA<N, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, t, tw);
+                fwdA<N, N1, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, t, tw);
         }
         __syncthreads();
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < NC * N)
-                fwdB<N, true, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, k1, tw);
+                fwdB<N, N1, true, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, k1, tw);
         }
     } else {
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < NC * N)
-                invB<N, true, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, k1, tw);
+                invB<N, N1, true, T>(sp + (long long)slab * N * H + col, H, buf + s * N * W + w, W, k1, tw);
         }
         __syncthreads();
         for (int it = tid; it < P * N2; it += NT) {
             const int pc = it % P, t = it / P;
             const int s = pc / W, w = pc - s * W, col = col0 + w, slab = slab0 + s;
             if (col < H && slab < NC * N)
-                invA<N, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, t, tw);
+                invA<N, N1, T>(buf + s * N * W + w, W, sp + (long long)slab * N * H + col, H, t, tw);
         }
     }
 }
@@ -482,13 +528,13 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
 // six components split over a lane pair duplicated n . tau n and needed
 // shuffles (at 243^3 the separate phase took P3 from 0.206 to 0.185 ms in
 // FP32 and from 7.4 to 6.2 ms in FP64).
-template <int N, typename T>
-__global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T3 <= 512)
-                                                      ? (Cfg<N, T>::T3 <= 256 ? 4 : 2)
+template <int N, typename T, int NA = Plan<N>::N1, int TV = 0>
+__global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T3, (sizeof(T) == 4 && Cfg<N, T, NA, TV>::T3 <= 512)
+                                                      ? (Cfg<N, T, NA, TV>::T3 <= 256 ? 4 : 2)
                                                       : is_dd_v<T> ? FFTG_DD_P3_MINB : 1) k_p3(PassArgs a) {
-    using C = Cfg<N, T>;
+    using C = Cfg<N, T, NA, TV>;
     constexpr int H = C::H, W = C::W3, NT = C::T3;
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N1 = NA, N2 = N / NA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf = tw + N;  // [6][N][W]
@@ -505,7 +551,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
     for (int it = tid; it < P * N2; it += NT) {
         const int pc = it % P, t = it / P;
         const int c = pc / W, w = pc - c * W, col = col0 + w;
-        if (col < H) fwdA<N, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
+        if (col < H) fwdA<N, N1, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
     }
     __syncthreads();
     const T scale = (T)a.scale;
@@ -517,7 +563,7 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+            if (col0 + w < H) fwdB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
         }
         __syncthreads();
     }
@@ -532,33 +578,33 @@ __global__ void __launch_bounds__(Cfg<N, T>::T3, (sizeof(T) == 4 && Cfg<N, T>::T
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
             const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+            if (col0 + w < H) invB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
         }
     }
     __syncthreads();
     for (int it = tid; it < P * N2; it += NT) {
         const int pc = it % P, t = it / P;
         const int c = pc / W, w = pc - c * W, col = col0 + w;
-        if (col < H) invA<N, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, t, tw);
+        if (col < H) invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, t, tw);
     }
 }
 
 // ----------------------------------------------------------------------- P5
 // T: FFT precision; TO: output real type (P5_RHS writes the CG residual r
 // in the inner precision).
-template <int N, typename T, int MODE, typename TO>
+template <int N, typename T, int MODE, typename TO, int NA = Plan<N>::N1, int TV = 0>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_dd_v<T> ? FFTG_DD_MINB : 2)
     k_p5(PassArgs a) {
-    using C = Cfg<N, T>;
+    using C = Cfg<N, T, NA, TV>;
     constexpr int R = C::R, H = C::H;
-    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    constexpr int N1 = NA, N2 = N / NA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* z = tw + N;  // [3][R][N]
     const int f = blockIdx.z;
     CGState* cg = a.cg ? a.cg + f : nullptr;
     if (a.active && !a.active[f]) return;
-    if (MODE == P5_DOT && cg->done) return;
+    if ((MODE == P5_DOT || MODE == P5_CGF) && cg->done) return;
     const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
     const int row0 = blockIdx.x * R;
@@ -592,8 +638,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
             const int it = tid + (r0 + u) * kThreads;
             if (r0 + u < NRL && it < nrows * H) {
                 const int row = it / H, k = it - row * H;
-                const int pk = perm_pos<N>(k);
-                const int pn = perm_pos<N>(k == 0 ? 0 : N - k);
+                const int pk = perm_pos<N, N1>(k);
+                const int pn = perm_pos<N, N1>(k == 0 ? 0 : N - k);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const cplx<T> a0 = A[u][c], b0 = B[u][c];
@@ -608,13 +654,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
     if (N2 > 1) {
         for (int it = tid; it < NP * N1; it += kThreads) {
             const int pc = it % NP, k1 = it / NP;
-            if (pc % R < nrows) invB<N, false, T>(z + pc * N, 1, z + pc * N, 1, k1, tw);
+            if (pc % R < nrows) invB<N, N1, false, T>(z + pc * N, 1, z + pc * N, 1, k1, tw);
         }
         __syncthreads();
     }
     for (int it = tid; it < NP * N2; it += kThreads) {
         const int pc = it % NP, t = it / NP;
-        if (pc % R < nrows) invA<N, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
+        if (pc % R < nrows) invA<N, N1, T>(z + pc * N, 1, z + pc * N, 1, t, tw);
     }
     __syncthreads();
     const long long cs = a.cs;
@@ -630,11 +676,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
     constexpr int NV = (R * N) / VO;
     constexpr int NRE = (NV + kThreads - 1) / kThreads;
     constexpr int PB = FFTG_P5_PB < NRE ? FFTG_P5_PB : NRE;
+    // P5_DOT: p; P5_CGF: r (updated in place, r -= alpha q)
     const TO* pin = (const TO*)a.aux + f * a.fstride;
+    TO* rout = MODE == P5_CGF ? (TO*)a.aux3 + f * a.fstride : nullptr;
+    const TO alpha = MODE == P5_CGF ? (TO)cg->alpha : TO(0);
 #pragma unroll
     for (int r0 = 0; r0 < NRE; r0 += PB) {
         TO pv[PB][6][VO];
-        if (MODE == P5_DOT) {
+        if (MODE == P5_DOT || MODE == P5_CGF) {
 #pragma unroll
             for (int u = 0; u < PB; ++u) {
                 const int j = tid + (r0 + u) * kThreads;
@@ -663,6 +712,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
                 qd[5][e] = z2.y;
 #pragma unroll
                 for (int c = 0; c < 6; ++c) q[c][e] = (TO)qd[c][e];
+            }
+            if (MODE == P5_CGF) {
+                // r -= alpha q, <r, r> (lanes past the grid update padding only)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+#pragma unroll
+                    for (int e = 0; e < VO; ++e) pv[u][c][e] -= alpha * q[c][e];
+                    stv<VO, TO>(rout + c * cs + v0, pv[u][c]);
+                }
+#pragma unroll
+                for (int e = 0; e < VO; ++e) {
+                    if (i0 + e < nel) {
+                        const TO re[6] = {pv[u][0][e], pv[u][1][e], pv[u][2][e], pv[u][3][e], pv[u][4][e], pv[u][5][e]};
+                        acc0 += (T)frob<TO>(re, re);
+                    }
+                }
+                continue;
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) stv<VO, TO>(out + c * cs + v0, q[c]);
@@ -700,6 +766,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
     if (tid != 0) return;
     if (MODE == P5_DOT)
         cg_after_dot(cg, tot[0]);
+    else if (MODE == P5_CGF)
+        cg_after_update(cg, tot[0]);
     else
         cg_start(cg, tot[0], tot[1]);
 }
@@ -714,6 +782,8 @@ enum PassKind : int {
     // double-float FFTs (the mixed path's residual): FP64 field in, FP32
     // residual or FP64 field out
     PK_P1_PLAIN_DD, PK_P2_DD, PK_P3_DD, PK_P4_DD, PK_P5_RHS_DD_TO_F32, PK_P5_PLAIN_DD_TO_F64,
+    // the CG iteration without the update pass (P1_CGF / P5_CGF), FP32
+    PK_P1_CGF_F32, PK_P5_CGF_F32,
     PK_COUNT
 };
 
@@ -781,6 +851,8 @@ cudaError_t run_pass_n(PassKind kind, const PassArgs& a, int nf, cudaStream_t s)
         case PK_P5_RHS_DD_TO_F32: return launch_k(k_p5<N, dd, P5_RHS, float>, r64, CDD::smem_rows, a, s);
         case PK_P5_PLAIN_DD_TO_F64:
             return launch_k(k_p5<N, dd, P5_PLAIN, double>, r64, CDD::smem_rows, a, s);
+        case PK_P1_CGF_F32: return launch_k(k_p1<N, float, P1_CGF>, r32, C32::smem_rows, a, s);
+        case PK_P5_CGF_F32: return launch_k(k_p5<N, float, P5_CGF, float>, r32, C32::smem_rows, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -332,6 +332,16 @@ int fftg_server_poll(fftg_server* s, fftg_result* out, int max, int* n, double w
     return s->error;
 }
 
+int fftg_server_cancel_pending(fftg_server* s, long long* cancelled) {
+    if (!s) return FFTG_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const long long n = (long long)(s->incoming.size() + s->pending.size());
+    s->incoming.clear();
+    s->pending.clear();
+    if (cancelled) *cancelled = n;
+    return s->error;
+}
+
 int fftg_server_info(fftg_server* s, long long* completed, long long* evictions, long long* restores,
                      int* max_concurrent, double* mean_batch) {
     if (!s) return FFTG_EINVAL;

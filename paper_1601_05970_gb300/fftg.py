@@ -137,6 +137,10 @@ SIGNATURES = {
     "fftg_launch_count": (C.c_longlong, [C.c_void_p]),
     "fftg_reset_state": (C.c_int, [C.c_void_p]),
     "fftg_probe_fma_rate": (C.c_int, [C.c_int, C.c_int, C.c_void_p, _D6]),
+    "fftg_schedule_set": (C.c_int, [C.c_int, C.c_int, C.c_int]),
+    "fftg_schedule_get": (C.c_int, [C.c_int, C.c_int]),
+    "fftg_schedule_describe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "fftg_autotune": (C.c_int, [C.c_int, C.c_int, C.c_void_p, _D6, C.POINTER(C.c_int)]),
     "fftg_workspace_size_batch": (C.c_int, [C.c_int, C.c_int, C.POINTER(fftg_options),
                                             C.POINTER(C.c_size_t)]),
     "fftg_create_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_uint8),
@@ -145,6 +149,11 @@ SIGNATURES = {
     "fftg_select_cell": (C.c_int, [C.c_void_p, C.c_int]),
     "fftg_batch_step": (C.c_int, [C.c_void_p, _D6, C.c_double, C.c_double, _D6,
                                   C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fftg_group_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]),
+    "fftg_group_step": (C.c_int, [C.c_void_p, _D6, C.POINTER(C.c_int), C.c_double, C.c_double, _D6,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fftg_group_launch_count": (C.c_longlong, [C.c_void_p]),
+    "fftg_group_destroy": (None, [C.c_void_p]),
     "fftg_server_clock": (C.c_double, []),
     "fftg_server_start": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
                                     C.POINTER(fftg_phase), C.POINTER(fftg_options), C.c_double,
@@ -405,6 +414,62 @@ class Cell:
         return q, pq.value
 
 
+class Group:
+    """Several batch handles (`Cell`s, one grid size each) that take their
+    increments together as one CUDA graph launch (fftg_group_*): Newton and
+    CG loops run on the device, the handles' branches concurrently. The
+    cells must outlive the group."""
+
+    def __init__(self, cells):
+        lib = load()
+        self.cells = list(cells)
+        arr = (C.c_void_p * len(self.cells))(*[c.h.value for c in self.cells])
+        h = C.c_void_p()
+        check(lib.fftg_group_create(C.byref(h), arr, len(self.cells)), "fftg_group_create")
+        self.h = h
+        self._lib = lib
+        self.sizes = [c.ncells for c in self.cells]
+
+    def step(self, dE, tol_newton, tol_cg, run=None):
+        """One increment for every cell: dE is a list with one [ncells, 6]
+        array per handle. Returns per handle (sigma [ncells, 6], newton,
+        cg, status)."""
+        tot = sum(self.sizes)
+        d = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).reshape(-1, 6) for x in dE]))
+        assert d.shape == (tot, 6)
+        sig = np.zeros((tot, 6))
+        nn = (C.c_int * tot)()
+        nc = (C.c_int * tot)()
+        st = (C.c_int * tot)()
+        rp = None
+        if run is not None:
+            r = np.concatenate([np.asarray(x, dtype=np.int32).reshape(-1) for x in run])
+            rp = (C.c_int * tot)(*[int(v) for v in r])
+        rc = self._lib.fftg_group_step(self.h, d.ctypes.data_as(_D6), rp, tol_newton, tol_cg,
+                                       sig.ctypes.data_as(_D6), nn, nc, st)
+        if rc not in (FFTG_OK, FFTG_ENOCONV_NEWTON, FFTG_ENAN):
+            check(rc, "fftg_group_step")
+        out, o = [], 0
+        for n in self.sizes:
+            out.append((sig[o:o + n], np.array(nn[o:o + n]), np.array(nc[o:o + n]), np.array(st[o:o + n])))
+            o += n
+        return out
+
+    def launch_count(self):
+        return self._lib.fftg_group_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.fftg_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching server for one grid size (fftg_server_* calls).
 
@@ -630,3 +695,41 @@ def fma_rate(precision="fp64", iters=1 << 16, stream=None):
     check(load().fftg_probe_fma_rate(FFTG_FP64 if precision == "fp64" else FFTG_MIXED, int(iters),
                                      C.c_void_p(st.cuda_stream), C.byref(out)), "fftg_probe_fma_rate")
     return out.value
+
+
+SCHED_KINDS = ("p1", "p2", "p3", "p4", "p5")
+SCHED_VARIANTS = 4
+FFTG_TUNE_CACHE = 1
+FFTG_TUNE_FORCE = 2
+
+
+def schedule_set(N, kind, variant):
+    """Select schedule `variant` of pass `kind` (0-4 or "p1".."p5") at grid N."""
+    k = SCHED_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    check(load().fftg_schedule_set(int(N), k, int(variant)), "fftg_schedule_set")
+
+
+def schedule_get(N):
+    """{kind: variant} in use at grid N."""
+    return {k: load().fftg_schedule_get(int(N), i) for i, k in enumerate(SCHED_KINDS)}
+
+
+def schedule_describe(N, kind, variant):
+    k = SCHED_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    sh = (C.c_int * 5)()
+    check(load().fftg_schedule_describe(int(N), k, int(variant), sh), "fftg_schedule_describe")
+    return dict(split=(sh[0], sh[1]), rows=sh[2], cols=sh[3], blocks=sh[4])
+
+
+def autotune(N, cache=True, force=False, stream=None):
+    """Time every schedule of the FP32 CG passes at grid N and select the
+    fastest. Returns ({kind: chosen variant}, {kind: [ms per variant]})."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ms = np.zeros(len(SCHED_KINDS) * SCHED_VARIANTS)
+    ch = (C.c_int * len(SCHED_KINDS))()
+    flags = (FFTG_TUNE_CACHE if cache else 0) | (FFTG_TUNE_FORCE if force else 0)
+    check(load().fftg_autotune(int(N), flags, C.c_void_p(st.cuda_stream), _dptr(ms), ch), "fftg_autotune")
+    return ({k: ch[i] for i, k in enumerate(SCHED_KINDS)},
+            {k: [float(v) for v in ms[i * SCHED_VARIANTS:(i + 1) * SCHED_VARIANTS]]
+             for i, k in enumerate(SCHED_KINDS)})

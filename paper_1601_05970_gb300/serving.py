@@ -25,7 +25,8 @@ from . import inputs as I
 
 
 def slots_for_budget(N, budget_bytes, precision="mixed", max_slots=32):
-    """Cells of grid N that fit in `budget_bytes` of device memory."""
+    """Cells of grid N that fit in `budget_bytes` of device memory (at least
+    one, at most max_slots), and the bytes of one more cell."""
     opt = fftg.default_options()
     opt.precision = fftg.FFTG_MIXED if precision == "mixed" else fftg.FFTG_FP64
     opt.nrhs_tangent = 0
@@ -51,23 +52,45 @@ def session_microstructure(N, session_id):
 
 
 def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
-        sessions_per_N=None, budget_gb=48.0, precision="mixed", seed=5,
-        tol_newton=1e-5, tol_cg=1e-8, max_requests=None):
+        sessions_per_N=None, budget_gb=None, precision="mixed", seed=5,
+        tol_newton=1e-5, tol_cg=1e-8, max_requests=None, drain_s=None, max_slots=64,
+        mem_fraction=0.5):
     """Poisson arrivals for `duration` seconds at `rate` requests/s.
+
+    Device memory: `budget_gb`, or by default `mem_fraction` of the device
+    memory free at the start, split between the grid sizes in proportion to
+    their request weights times their footprint per cell, so that each size
+    gets cells in proportion to its share of the requests (at most
+    `max_slots` per size). A request is admitted when a cell of its size is
+    free; a resident idle session is evicted to host memory only when every
+    cell of the size is taken.
+
+    After the arrivals stop, requests still queued get `drain_s` seconds
+    (default: `duration`) to be admitted; then the queues are cancelled and
+    the requests in flight finish. Above the servers' capacity that backlog
+    is reported (`backlog`, `saturated`), and a latency percentile that the
+    cancelled requests would decide is reported as None.
 
     Returns a dict with solves/s, p50/p95/p99 latency (ms), per-size counts
     and server statistics.
     """
+    import torch
     weights = np.asarray(weights, dtype=float) / np.sum(weights)
-    budget = budget_gb * 1e9
+    if budget_gb is None:
+        free, _ = torch.cuda.mem_get_info()
+        budget = mem_fraction * free
+    else:
+        budget = budget_gb * 1e9
+    per_cell = {N: slots_for_budget(N, 0, precision)[1] for N in Ns}
+    wb = sum(w * per_cell[N] for N, w in zip(Ns, weights))
     servers, slot_info = {}, {}
     for N, w in zip(Ns, weights):
-        slots, per = slots_for_budget(N, budget * w, precision)
+        slots, per = slots_for_budget(N, budget * w * per_cell[N] / wb, precision, max_slots)
         servers[N] = fftg.Server(N, slots, I.TWO_PHASE, precision=precision,
                                  tol_newton=tol_newton, tol_cg=tol_cg)
         slot_info[N] = dict(slots=slots, bytes_per_slot=per)
     if sessions_per_N is None:
-        sessions_per_N = {N: 2 * slot_info[N]["slots"] for N in Ns}
+        sessions_per_N = {N: min(2 * slot_info[N]["slots"], 64) for N in Ns}
     # sessions and microstructures are made before the clock starts
     sess = {}
     sid = 0
@@ -128,6 +151,28 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
         servers[N].submit(i, s_id, dE, phase)
         submitted += 1
     t_sub_end = fftg.Server.clock()
+    drain = duration if drain_s is None else drain_s
+    while fftg.Server.clock() - t_sub_end < drain:
+        with lock:
+            if not any(len(pending[N]) for N in Ns):
+                break
+        time.sleep(0.01)
+    cancelled = 0
+    for N, srv in servers.items():
+        c = srv.cancel_pending()
+        cancelled += c
+    # the cancelled requests give no result: the collector stops waiting
+    # for them once only they are left
+    t_cancel = fftg.Server.clock()
+    while True:
+        with lock:
+            n_left = sum(len(pending[N]) for N in Ns)
+        if n_left <= cancelled or fftg.Server.clock() - t_cancel > 120.0:
+            break
+        time.sleep(0.01)
+    with lock:
+        for N in Ns:
+            pending[N].clear()
     stop.set()
     th.join()
     t_end = fftg.Server.clock()
@@ -136,6 +181,17 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
         srv.stop()
     lat = np.array([r["t_done"] - r["t_submit"] for r in results]) * 1e3
     ok = sum(1 for r in results if r["status"] == 0)
+    # a percentile is known when the cancelled requests (latency above any
+    # completed one) cannot reach it
+    total = len(results) + cancelled
+
+    def pct(q):
+        if not lat.size:
+            return None
+        if cancelled == 0:
+            return float(np.percentile(lat, q))
+        rank = int(math.ceil(q / 100.0 * total))   # nearest rank among all requests
+        return float(np.sort(lat)[rank - 1]) if rank <= lat.size else None
     per_N = {}
     for N in Ns:
         l = np.array([r["t_done"] - r["t_submit"] for r in results if sess[r["session_id"]][0] == N]) * 1e3
@@ -145,12 +201,10 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
                         evictions=infos[N]["evictions"], max_concurrent=infos[N]["max_concurrent"],
                         mean_batch=round(infos[N]["mean_batch"], 2))
     return dict(rate=rate, duration_s=round(t_sub_end - t0, 3), requests=submitted,
-                completed=len(results), ok=ok,
+                completed=len(results), ok=ok, backlog=cancelled, saturated=cancelled > 0,
                 solves_per_s=len(results) / max(t_end - t0, 1e-9),
-                p50_ms=float(np.percentile(lat, 50)) if lat.size else None,
-                p95_ms=float(np.percentile(lat, 95)) if lat.size else None,
-                p99_ms=float(np.percentile(lat, 99)) if lat.size else None,
-                per_N=per_N, precision=precision, budget_gb=budget_gb)
+                p50_ms=pct(50), p95_ms=pct(95), p99_ms=pct(99),
+                per_N=per_N, precision=precision, budget_gb=round(budget / 1e9, 1))
 
 
 def batched_workload(n_rve=256, Ns=(15, 27, 45, 75), seed=1000):
@@ -168,10 +222,15 @@ def batched_workload(n_rve=256, Ns=(15, 27, 45, 75), seed=1000):
     return rves
 
 
-def run_batched(rves, n_inc=5, precision="mixed", tol_newton=1e-5, tol_cg=1e-8):
+def run_batched(rves, n_inc=5, precision="mixed", tol_newton=1e-5, tol_cg=1e-8, graph=True):
     """All RVEs of one grid size form one batch handle (one launch per pass
-    for the whole group); the groups run concurrently, each on its own stream
-    from its own host thread. Returns RVE solves/s and per-group counts."""
+    for the whole group of that size).
+
+    graph=True: the handles of all sizes form one fftg_group, and each
+    increment of every RVE is ONE CUDA graph launch (Newton and CG loops on
+    the device, the sizes' branches concurrent). graph=False: each size is
+    driven from its own host thread and stream (a host round trip per Newton
+    iteration). Returns RVE solves/s and per-size counts."""
     import torch
     groups = {}
     for i, r in enumerate(rves):
@@ -183,6 +242,29 @@ def run_batched(rves, n_inc=5, precision="mixed", tol_newton=1e-5, tol_cg=1e-8):
         cells[N] = fftg.Cell(N, ph, I.TWO_PHASE, precision=precision, nrhs_tangent=0,
                              stream=streams[N])
     out = {N: dict(cells=len(idx), newton=0, cg=0, failed=0, seconds=0.0) for N, idx in groups.items()}
+    if graph:
+        Ns = sorted(groups)
+        grp = fftg.Group([cells[N] for N in Ns])
+        dEs = [np.stack([rves[i]["dE"] for i in groups[N]]) for N in Ns]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_inc):
+            res = grp.step(dEs, tol_newton, tol_cg)
+            for N, (sig, nn, nc, st) in zip(Ns, res):
+                out[N]["newton"] += int(nn.sum())
+                out[N]["cg"] += int(nc.sum())
+                out[N]["failed"] += int((st != 0).sum())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        launches = grp.launch_count()
+        grp.close()
+        for c in cells.values():
+            c.close()
+        n = len(rves) * n_inc
+        return dict(rves=len(rves), increments=n_inc, solves=n, seconds=wall, solves_per_s=n / wall,
+                    groups={str(N): v for N, v in sorted(out.items())}, precision=precision,
+                    mode="one graph launch per increment for all sizes", graph_launches=n_inc,
+                    kernel_launches=launches)
 
     def work(N):
         idx = groups[N]
@@ -210,7 +292,7 @@ def run_batched(rves, n_inc=5, precision="mixed", tol_newton=1e-5, tol_cg=1e-8):
     n = len(rves) * n_inc
     return dict(rves=len(rves), increments=n_inc, solves=n, seconds=wall,
                 solves_per_s=n / wall, groups={str(N): v for N, v in sorted(out.items())},
-                precision=precision)
+                precision=precision, mode="one host thread and stream per size")
 
 
 def main(argv=None):
@@ -220,7 +302,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="continuous-batching RVE serving sweep")
     ap.add_argument("--rates", default="50,100,200,500")
     ap.add_argument("--seconds", type=float, default=10.0)
-    ap.add_argument("--budget-gb", type=float, default=48.0)
+    ap.add_argument("--budget-gb", type=float, default=None,
+                    help="device memory for the cells (default: half of the free memory)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args(argv)
     fftg.load()

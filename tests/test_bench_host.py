@@ -42,3 +42,31 @@ def test_captured_traffic_is_kept_only_for_its_sources(monkeypatch):
         monkeypatch.setattr(bench, "TRAFFIC", changed)
         assert bench.measured_traffic(kind, tr["N"]) is None
         monkeypatch.undo()
+
+
+def test_fft_flop_model_counts_the_pencil_plans():
+    # radix-3 and radix-5 butterflies (16 and 48 real flops), complex
+    # twiddle products (6): a 15-point pencil is 5 radix-3 butterflies,
+    # (3-1)(5-1) twiddles and 3 radix-5 butterflies; a 243 = 27 x 9 pencil
+    # has 405 radix-3 butterflies and 568 twiddle products
+    assert bench.fft_flops(3) == 16 and bench.fft_flops(5) == 48
+    assert bench.fft_flops(15) == 5 * 16 + 8 * 6 + 3 * 48
+    assert bench.fft_flops(243) == 405 * 16 + 568 * 6
+    f = bench.flops_per_voxel(243)
+    assert 850 < sum(f.values()) < 950
+
+
+def test_cg_roofline_from_kernel_times():
+    # 243^3: 100 CG field-iterations, 5 Newton projections, one tangent
+    # (12 extra field launches of P2-P4 in FP32); every kernel at 1 ms per
+    # field launch gives its algorithmic bytes per millisecond
+    V = 243 ** 3
+    eff = {"p1_cg": 100, "p5_dot": 100, "cg_update": 100, "p2": 117, "p3": 117, "p4": 117}
+    prof = {k + "_f32": (float(n), n + 3) for k, n in eff.items()}
+    rf = bench.cg_roofline(prof, 243, 100, 5, 1, "_f32", hbm=1000.0)
+    b = bench.bytes_per_voxel(243)
+    for k in eff:
+        assert rf["kernels"][k]["ms"] == 1.0
+        assert abs(rf["kernels"][k]["GB/s"] - b[k + "_f32"] * V / 1e-3 / 1e9) < 0.1
+    assert rf["matvec"]["ms_per_field_iter"] == 5.0 and rf["iteration"]["ms_per_field_iter"] == 6.0
+    assert abs(rf["iteration"]["bytes_per_voxel"] - 460.8) < 0.2
