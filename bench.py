@@ -369,9 +369,10 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- ranks
-def rank_seed(rank):
-    """Each rank solves its own cell: the microstructure seed of rank r."""
-    return 2 + 1000 * rank
+def rank_seed(rank, base=2):
+    """Each rank solves its own cell: the microstructure seed of rank r
+    (base: the workload's own seed, 2 at 243^3 and 1 at 135^3)."""
+    return base + 1000 * rank
 
 
 def reduce_over_ranks(dist, dev_ms, wall_ms, units, launches, device):
@@ -755,7 +756,7 @@ def main():
         for n in dict.fromkeys(grids):
             chosen, ms = fftg.autotune(n, cache=True)
             tuned[n] = {"chosen": chosen, "ms": ms}
-    w = I.workload("spheres243" if N == 243 else "spheres135", seed=rank_seed(rank))
+    w = I.workload("spheres243" if N == 243 else "spheres135", seed=rank_seed(rank, 2 if N == 243 else 1))
     path = w["dE"]
     tol_nw, tol_cg = w["tol_newton"], w["tol_cg"]
     tangent = not args.no_tangent

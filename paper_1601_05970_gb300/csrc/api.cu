@@ -406,16 +406,20 @@ static PassArgs base_args_fft(fftg_handle* h, int prec) {
     return a;
 }
 
-static int run_p234(fftg_handle* h, int prec, double scale, CGState* cg, int nf, const int* mask) {
+static int run_p234(fftg_handle* h, int prec, double scale, CGState* cg, int nf, const int* mask,
+                    const double* red_in = nullptr, int red_n = 0) {
     PassArgs a = base_args_fft(h, prec);
     a.out = h->spec;
     a.cg = cg;
     a.scale = scale;
     a.active = mask;
+    a.red_in = red_in;
+    a.red_n = red_n;
     const PassKind k2 = prec == FFT_DD ? PK_P2_DD : prec == FFT_F64 ? PK_P2_F64 : PK_P2_F32;
     const PassKind k3 = prec == FFT_DD ? PK_P3_DD : prec == FFT_F64 ? PK_P3_F64 : PK_P3_F32;
     const PassKind k4 = prec == FFT_DD ? PK_P4_DD : prec == FFT_F64 ? PK_P4_F64 : PK_P4_F32;
     CK(pass(h, k2, a, nf));
+    a.red_in = nullptr;
     CK(pass(h, k3, a, nf));
     CK(pass(h, k4, a, nf));
     return FFTG_OK;
@@ -468,7 +472,9 @@ static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long
         a.out = h->spec;
         a.cg = h->cg;
         CK(pass(h, PK_P1_CGF_F32, a, nf));
-        int rc = run_p234(h, FFT_F32, invN3, h->cg, nf, nullptr);
+        // P2 reduces P1's block partials of <p, C : p> (alpha)
+        const int nb1 = variant_shape(h->N, TK_P1, schedule_variant(h->N, TK_P1)).blocks;
+        int rc = run_p234(h, FFT_F32, invN3, h->cg, nf, nullptr, h->partials, nb1);
         if (rc) return rc;
         PassArgs b = base_args(h, false);
         b.in = h->spec;

@@ -160,6 +160,22 @@ __device__ __forceinline__ double block_sum(double v) {
     return total;
 }
 
+// Sum over a block of any size up to 1024 threads (1D), in a fixed order
+// (lanes by shuffles, then the warps in index order); result in thread 0.
+__device__ __forceinline__ double block_sum_any(double v) {
+    __shared__ double red_any[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red_any[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) s += red_any[w];
+    return s;
+}
+
 // Store this block's NV partial sums and report whether this block is the
 // last one of `nblocks` to do so. Partials of the other blocks are then
 // visible to it (fence before the ticket).

@@ -531,11 +531,15 @@ FsPointArgs point_args(fftg_fs_handle* h) {
 }
 
 // Spectrum passes P2, P3 (scale on Ghat), P4.
-int fs_p234(fftg_fs_handle* h, int prec, double scale, CGState* cg) {
+int fs_p234(fftg_fs_handle* h, int prec, double scale, CGState* cg, const double* red_in = nullptr,
+            int red_n = 0) {
     FsArgs a = fs_args(h, prec);
     a.cg = cg;
     a.scale = scale;
+    a.red_in = red_in;
+    a.red_n = red_n;
     CK(fs_pass(h, prec == FFT_DD ? FK_P2_DD : prec == FFT_F64 ? FK_P2_F64 : FK_P2_F32, a));
+    a.red_in = nullptr;
     CK(fs_pass(h, prec == FFT_DD ? FK_P3_DD : prec == FFT_F64 ? FK_P3_F64 : FK_P3_F32, a));
     CK(fs_pass(h, prec == FFT_DD ? FK_P4_DD : prec == FFT_F64 ? FK_P4_F64 : FK_P4_F32, a));
     return FFTG_OK;
@@ -599,7 +603,8 @@ int fs_cg_iteration(fftg_fs_handle* h) {
         a.aux3 = h->x;
         a.cg = h->cg;
         CK(fs_pass(h, FK_P1_CGF_F32, a));
-        int rc = fs_p234(h, FFT_F32, invN3, h->cg);
+        // P2 reduces P1's block partials of <p, K : p> (alpha)
+        int rc = fs_p234(h, FFT_F32, invN3, h->cg, h->partials, fs_row_blocks(h->N, false));
         if (rc) return rc;
         FsArgs b = fs_args(h, FFT_F32);
         b.in = h->spec;

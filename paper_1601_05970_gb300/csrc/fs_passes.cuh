@@ -50,6 +50,8 @@ struct FsArgs {
     double scale;          // P3: factor on Ghat (+-1/N^3)
     long long cs;          // component stride of the real fields (elements)
     int unit;              // P1_TANRHS: tau = K : E_unit, E_unit the unit tensor at component unit
+    const double* red_in;  // P2 of the fused CG iteration: P1's block partials of <p, K : p>
+    int red_n;             // (reduced by P2's first block, which sets alpha)
 };
 
 // Tuning: voxels per lane in the elementwise phases of P1 and P5 (moved as
@@ -285,7 +287,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
             z[4 * R * N + i0 + e] = mk(s[8][e], T(0));
         }
     }
+    // FS_P1_CGF: this block's part of <p, K : p> (P2 reduces the parts)
+    __shared__ double pkp_warp[kThreads / 32];
+    if (MODE == FS_P1_CGF) {
+        const double wv = warp_sum((double)pkp);
+        if ((tid & 31) == 0) pkp_warp[tid >> 5] = wv;
+    }
     __syncthreads();
+    if (MODE == FS_P1_CGF && tid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += pkp_warp[w];
+        a.partials[blockIdx.x] = t;
+    }
     constexpr int NP = kFsPairs * R;
     for (int it = tid; it < NP * N2; it += kThreads) {
         const int pc = it % NP, t = it / NP;
@@ -317,16 +331,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
                 out[(2 * c + 1) * HS + o] = mk(T(0.5) * d.y, T(-0.5) * d.x);
             }
         }
-    }
-    if (MODE == FS_P1_CGF) {
-        // alpha = <r, r> / <p, K : p>
-        CGState* cg = a.cg;
-        const int nb = gridDim.x;
-        double part[1] = {block_sum((double)pkp)};
-        if (!publish_partials<1>(part, a.partials, blockIdx.x, nb, &cg->ticket)) return;
-        double tot[1];
-        reduce_partials<1>(a.partials, nb, &cg->ticket, tot);
-        if (tid == 0) cg_after_dot(cg, tot[0]);
     }
 }
 
@@ -601,6 +605,8 @@ static cudaError_t launch_fs_p24(const FsArgs& a, cudaStream_t s) {
     b.out = a.out;
     b.cg = a.cg;
     b.tw = a.tw;
+    b.red_in = a.red_in;
+    b.red_n = a.red_n;
     const dim3 g((C::H + C::W2 - 1) / C::W2, (kFsComp * N + C::S2 - 1) / C::S2, 1);
     cudaError_t e = cudaFuncSetAttribute(k_p24<N, T, FWD, kFsComp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_p24);

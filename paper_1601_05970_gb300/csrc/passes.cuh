@@ -59,6 +59,11 @@ struct PassArgs {
     long long sstride;     // spectrum stride between fields (complex elements)
     long long tstride;     // tangent stride between fields (0: shared)
     const int* active;     // per field: 0 = skip this field (null: all run)
+    // P2 of the fused CG iteration: the block partials of <p, C : p> that P1
+    // wrote ([nf][red_n]); block (0, 0) of each field reduces them in a
+    // fixed order and sets alpha (null: nothing to reduce)
+    const double* red_in;
+    int red_n;
 };
 
 // Tuning of the elementwise phases of P1 and P5: voxels per lane (1, 2 or 4,
@@ -392,7 +397,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
             z[2 * R * N + i0 + e] = mk(s[4][e], s[5][e]);
         }
     }
+    // P1_CGF: this block's part of <p, C : p>, lanes by shuffles, warps in
+    // index order after the barrier below; P2 reduces the blocks' parts (no
+    // fence or ticket at the end of every block here)
+    __shared__ double pcp_warp[kThreads / 32];
+    if (MODE == P1_CGF) {
+        const double wv = warp_sum((double)pcp);
+        if ((tid & 31) == 0) pcp_warp[tid >> 5] = wv;
+    }
     __syncthreads();
+    if (MODE == P1_CGF && tid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += pcp_warp[w];
+        a.partials[(size_t)f * gridDim.x + blockIdx.x] = t;
+    }
     constexpr int NP = 3 * R;
     for (int it = tid; it < NP * N2; it += kThreads) {
         const int pc = it % NP, t = it / NP;
@@ -423,17 +442,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
             out[(2 * c + 1) * HS + o] = B;
         }
     }
-    if (MODE == P1_CGF) {
-        // alpha = <r, r> / <p, C : p> (see P1_CGF above)
-        CGState* cg = a.cg + f;
-        const int nb = gridDim.x;
-        double part[1] = {block_sum((double)pcp)};
-        double* partials = a.partials + (size_t)f * nb;
-        if (!publish_partials<1>(part, partials, blockIdx.x, nb, &cg->ticket)) return;
-        double tot[1];
-        reduce_partials<1>(partials, nb, &cg->ticket, tot);
-        if (tid == 0) cg_after_dot(cg, tot[0]);
-    }
 }
 
 // -------------------------------------------------------------- P2 / P4 (x2)
@@ -452,6 +460,16 @@ __global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T2) k_p24(PassArgs a) {
     if (a.active && !a.active[f]) return;
     if (a.cg && a.cg[f].done) return;
     const int tid = threadIdx.x;
+    if (a.red_in && blockIdx.x == 0 && blockIdx.y == 0) {
+        // alpha = <r, r> / <p, C : p> of the fused CG iteration, from the
+        // block partials of P1 (thread t takes blocks t, t + NT, ...; then
+        // a fixed tree), before this block's share of the transform
+        const double* in = a.red_in + (size_t)f * a.red_n;
+        double acc = 0.0;
+        for (int b = tid; b < a.red_n; b += NT) acc += in[b];
+        acc = block_sum_any(acc);
+        if (tid == 0) cg_after_dot(a.cg + f, acc);
+    }
     load_tw<T>(tw, a.tw, N);
     __syncthreads();
     const int col0 = blockIdx.x * W, slab0 = blockIdx.y * S;
