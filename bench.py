@@ -70,6 +70,7 @@ def bytes_per_voxel(N):
         # dot <p, C:p>), P5 reads the spectrum and r and writes r
         "p1_cgf_f32": 5 * 24 + 28 + s32,
         "p5_cgf_f32": s32 + 24 + 24,
+        "cg_rr_f32": 0.0,                          # block partials only
         "p1_tanrhs_f32": 28 + s32,
         "p5_rhs_f32_to_f32": s32 + 24,
         "p1_cg_f64": 5 * 48 + 56 + s64,
@@ -84,7 +85,7 @@ def bytes_per_voxel(N):
 # (FP64 path, basic scheme) and without it (mixed path).
 CG_KINDS = ("p1_cg", "p2", "p3", "p4", "p5_dot", "cg_update")
 MATVEC_KINDS = ("p1_cg", "p2", "p3", "p4", "p5_dot")
-CGF_KINDS = ("p1_cgf", "p2", "p3", "p4", "p5_cgf")
+CGF_KINDS = ("p1_cgf", "p2", "p3", "p4", "p5_cgf", "cg_rr")
 
 # Pencil plans N = N1 x N2 of the FFT passes (the register DFT of N1 points,
 # then of N2 points).
@@ -475,8 +476,8 @@ def cg_roofline(prof, N, field_iters, projections, tangent_calls, sfx="_f32", hb
     bpv = bytes_per_voxel(N)
     V = N ** 3
     fused = ("p1_cgf" + sfx) in prof
-    kinds, mv_kinds = (CGF_KINDS, CGF_KINDS) if fused else (CG_KINDS, MATVEC_KINDS)
-    eff = {k: field_iters for k in ("p1_cg", "p5_dot", "cg_update", "p1_cgf", "p5_cgf")}
+    kinds, mv_kinds = (CGF_KINDS, CGF_KINDS[:5]) if fused else (CG_KINDS, MATVEC_KINDS)
+    eff = {k: field_iters for k in ("p1_cg", "p5_dot", "cg_update", "p1_cgf", "p5_cgf", "cg_rr")}
     for k in ("p2", "p3", "p4"):
         eff[k] = field_iters + projections + (12 if sfx == "_f32" else 6) * tangent_calls
     kern = {}
@@ -489,6 +490,8 @@ def cg_roofline(prof, N, field_iters, projections, tangent_calls, sfx="_f32", hb
         gbs = b * V / (ms * 1e-3) / 1e9
         kern[base] = {"ms": round(ms, 4), "bytes_per_voxel": round(b, 1), "GB/s": round(gbs, 1),
                       "frac": round(gbs / hbm, 3)}
+    if fused and "cg_rr" not in kern:          # older builds: the reduction ran in P5
+        kinds = kinds[:5]
 
     def agg(kinds, what):
         if not all(k in kern for k in kinds):
@@ -548,7 +551,8 @@ def fs_bytes_per_voxel(N):
             "fs_p5_dot_f32": s32 + 36 + 36, "fs_cg_update_f32": 3 * 36,
             # without the update pass: P1 as above (and <p, K:p>); P5 reads
             # the spectrum and r and writes r
-            "fs_p1_cgf_f32": 5 * 36 + 36 + 1 + s32, "fs_p5_cgf_f32": s32 + 36 + 36}
+            "fs_p1_cgf_f32": 5 * 36 + 36 + 1 + s32, "fs_p5_cgf_f32": s32 + 36 + 36,
+            "fs_cg_rr_f32": 0.0}
 
 
 def finite_strain_line(N=243, warm=1, timed=2):
@@ -596,7 +600,7 @@ def finite_strain_line(N=243, warm=1, timed=2):
     it = nc_tot + nt_tot  # CG iterations of the Newton and of the tangent solves
     solves = nn_tot + 9 * timed
     eff = {"fs_p1_cg_f32": it, "fs_p5_dot_f32": it, "fs_cg_update_f32": it,
-           "fs_p1_cgf_f32": it, "fs_p5_cgf_f32": it,
+           "fs_p1_cgf_f32": it, "fs_p5_cgf_f32": it, "fs_cg_rr_f32": it,
            "fs_p2_f32": it + solves + 9 * timed, "fs_p3_f32": it + solves + 9 * timed,
            "fs_p4_f32": it + solves + 9 * timed}
     kind, (kms, kn) = max(((k, v) for k, v in prof.items() if k in bpv), key=lambda kv: kv[1][0])
@@ -604,7 +608,8 @@ def finite_strain_line(N=243, warm=1, timed=2):
     alg = eff[kind] * V * bpv[kind]
     achieved = alg / (kms * 1e-3) / 1e9
     fused = "fs_p1_cgf_f32" in prof
-    it_kinds = (("fs_p1_cgf_f32", "fs_p2_f32", "fs_p3_f32", "fs_p4_f32", "fs_p5_cgf_f32") if fused else
+    it_kinds = (("fs_p1_cgf_f32", "fs_p2_f32", "fs_p3_f32", "fs_p4_f32", "fs_p5_cgf_f32", "fs_cg_rr_f32")
+                if fused else
                 ("fs_p1_cg_f32", "fs_p2_f32", "fs_p3_f32", "fs_p4_f32", "fs_p5_dot_f32", "fs_cg_update_f32"))
     iteration = None
     if all(k in prof and eff[k] for k in it_kinds):

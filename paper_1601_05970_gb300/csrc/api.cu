@@ -94,7 +94,7 @@ namespace {
 enum : int {
     KK_CONSTITUTIVE_F32 = PK_COUNT, KK_CONSTITUTIVE_F64, KK_CG_UPDATE_F32, KK_CG_UPDATE_F64,
     KK_NEWTON_UPDATE_F32, KK_NEWTON_UPDATE_F64, KK_TANGENT_FLOOR, KK_TANGENT_AVERAGE,
-    KK_CG_FINISH_F32, KK_CG_FINISH_F64, KK_TANGENT_BOUNDS, KK_COUNT
+    KK_CG_FINISH_F32, KK_CG_FINISH_F64, KK_TANGENT_BOUNDS, KK_CG_RR, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "p1_plain_f64", "p1_plain_f32", "p1_tan_f64", "p1_tan_f32", "p1_cg_f64", "p1_cg_f32",
@@ -104,7 +104,7 @@ const char* const kKindNames[KK_COUNT] = {
     "p5_rhs_dd_to_f32", "p5_plain_dd_to_f64", "p1_cgf_f32", "p5_cgf_f32", "constitutive_f32",
     "constitutive_f64",
     "cg_update_f32", "cg_update_f64", "newton_update_f32", "newton_update_f64", "tangent_floor",
-    "tangent_average", "cg_finish_f32", "cg_finish_f64", "tangent_bounds"};
+    "tangent_average", "cg_finish_f32", "cg_finish_f64", "tangent_bounds", "cg_rr_f32"};
 
 // Ring of event pairs around the handle's launches; drained at every read.
 struct Prof {
@@ -482,6 +482,12 @@ static int launch_cg_iteration(fftg_handle* h, int nf, const void* tangent, long
         b.aux3 = h->r;
         b.cg = h->cg;
         CK(pass(h, PK_P5_CGF_F32, b, nf));
+        // <r, r> from P5's block partials: beta and the stopping tests
+        const int nb5 = variant_shape(h->N, TK_P5, schedule_variant(h->N, TK_P5)).blocks;
+        const int slot = prof_begin(h, KK_CG_RR);
+        k_cg_rr<<<nf, 1024, 0, h->stream>>>(h->partials, nb5, h->cg);
+        prof_end(h, slot);
+        CK(cudaGetLastError());
         return FFTG_OK;
     }
     PassArgs a = base_args(h, f64);
@@ -715,7 +721,7 @@ static int run_cg(fftg_handle* h, int nf, const void* tangent, long long tstride
             CK(cudaStreamSynchronize(h->stream));
             int maxit = 0;
             for (int f = 0; f < nf; ++f) maxit = std::max(maxit, h->h_cg[f].it);
-            h->launches += (cg_fused(h) ? 6LL : 7LL) * (maxit + 1);
+            h->launches += 7LL * (maxit + 1);
             return FFTG_OK;
         }
         h->graphs_broken = true;
@@ -1310,7 +1316,7 @@ int fftg_group_step(fftg_group* g, const double* dE, const int* run, double tol_
         // update; per Newton pass 15 outside the CG loop; per CG loop pass
         // the iteration's kernels and the loop test (an upper bound when
         // the cells' CG counts differ between Newton passes)
-        const long long per_cg = cg_fused(h) ? 6 : 7;
+        const long long per_cg = 7;
         h->launches += 4 + 15LL * max_newton + (per_cg + 1) * (max_cg + max_newton);
         g->launches += 4 + 15LL * max_newton + (per_cg + 1) * (max_cg + max_newton);
     }

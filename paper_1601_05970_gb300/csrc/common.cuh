@@ -176,6 +176,19 @@ __device__ __forceinline__ double block_sum_any(double v) {
     return s;
 }
 
+// <r, r> of the fused CG iteration from the block partials P5 wrote
+// ([nf][nb], one per block): one block per field sums them in a fixed order
+// and takes the CG state's update step (beta and the stopping tests).
+static __global__ void __launch_bounds__(1024) k_cg_rr(const double* partials, int nb, CGState* cg) {
+    const int f = blockIdx.x;
+    if (cg[f].done) return;
+    const double* in = partials + (size_t)f * nb;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += in[b];
+    acc = block_sum_any(acc);
+    if (threadIdx.x == 0) cg_after_update(cg + f, acc);
+}
+
 // Store this block's NV partial sums and report whether this block is the
 // last one of `nblocks` to do so. Partials of the other blocks are then
 // visible to it (fence before the ticket).

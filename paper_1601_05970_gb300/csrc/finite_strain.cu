@@ -325,7 +325,7 @@ namespace {
 enum : int {
     FSK_CONSTITUTIVE_F32 = FK_COUNT, FSK_CONSTITUTIVE_F64, FSK_CG_UPDATE_F32, FSK_CG_UPDATE_F64,
     FSK_CG_FINISH_F32, FSK_CG_FINISH_F64, FSK_NEWTON_UPDATE_F32, FSK_NEWTON_UPDATE_F64, FSK_TANGENT_FLOOR,
-    FSK_TANGENT_AVERAGE, FSK_COUNT
+    FSK_TANGENT_AVERAGE, FSK_CG_RR, FSK_COUNT
 };
 const char* const kFsKindNames[FSK_COUNT] = {
     "fs_p1_plain_f64", "fs_p1_plain_f32", "fs_p1_tan_f64", "fs_p1_tan_f32", "fs_p1_cg_f64", "fs_p1_cg_f32",
@@ -336,7 +336,7 @@ const char* const kFsKindNames[FSK_COUNT] = {
     "fs_p5_rhs_f32_to_f32", "fs_p1_cgf_f32", "fs_p5_cgf_f32",
     "fs_constitutive_f32", "fs_constitutive_f64", "fs_cg_update_f32", "fs_cg_update_f64",
     "fs_cg_finish_f32", "fs_cg_finish_f64", "fs_newton_update_f32", "fs_newton_update_f64",
-    "fs_tangent_floor", "fs_tangent_average"};
+    "fs_tangent_floor", "fs_tangent_average", "fs_cg_rr_f32"};
 
 // Iterations without a new minimum of <r, r> after which an FP32 inner
 // solve counts as stagnated (as in the small-strain driver).
@@ -612,6 +612,11 @@ int fs_cg_iteration(fftg_fs_handle* h) {
         b.aux3 = h->r;
         b.cg = h->cg;
         CK(fs_pass(h, FK_P5_CGF_F32, b));
+        // <r, r> from P5's block partials: beta and the stopping tests
+        const int slot = fs_prof_begin(h, FSK_CG_RR);
+        k_cg_rr<<<1, 1024, 0, h->stream>>>(h->partials, fs_row_blocks(h->N, false), h->cg);
+        fs_prof_end(h, slot);
+        CK(cudaGetLastError());
         return FFTG_OK;
     }
     FsArgs a = fs_args(h, prec);
@@ -713,7 +718,7 @@ int fs_run_cg(fftg_fs_handle* h) {
             if (rc) return rc;
             CK(cudaMemcpyAsync(h->h_cg, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
-            h->launches += (fs_cg_fused(h) ? 6LL : 7LL) * (h->h_cg->it + 1);  // one of each per loop pass
+            h->launches += 7LL * (h->h_cg->it + 1);  // one of each per loop pass
             return FFTG_OK;
         }
     }

@@ -553,6 +553,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
     const int nb = gridDim.x;
     double part[2];
     part[0] = block_sum((double)acc0);
+    if (MODE == FS_P5_CGF) {
+        // the block's part of <r, r> (k_cg_rr reduces the parts)
+        if (tid == 0) a.partials[blockIdx.x] = part[0];
+        return;
+    }
     part[1] = (MODE == FS_P5_RHS) ? block_sum(acc1) : 0.0;
     if (!publish_partials<2>(part, a.partials, blockIdx.x, nb, &cg->ticket)) return;
     double tot[2];
@@ -560,8 +565,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P5_MINB : 1
     if (tid != 0) return;
     if (MODE == FS_P5_DOT)
         cg_after_dot(cg, tot[0]);
-    else if (MODE == FS_P5_CGF)
-        cg_after_update(cg, tot[0]);
     else
         cg_start(cg, tot[0], tot[1]);
 }

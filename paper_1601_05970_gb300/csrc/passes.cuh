@@ -776,6 +776,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
     const int nb = gridDim.x;
     double part[2];
     part[0] = block_sum((double)acc0);
+    if (MODE == P5_CGF) {
+        // the block's part of <r, r>; k_cg_rr reduces the parts (no fence
+        // or ticket at the end of every block here)
+        if (tid == 0) a.partials[(size_t)f * nb + blockIdx.x] = part[0];
+        return;
+    }
     part[1] = (MODE == P5_RHS) ? block_sum(acc1) : 0.0;
     double* partials = a.partials + (size_t)f * nb * 2;
     if (!publish_partials<2>(part, partials, blockIdx.x, nb, &cg->ticket)) return;
@@ -784,8 +790,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P5_MINB : is_d
     if (tid != 0) return;
     if (MODE == P5_DOT)
         cg_after_dot(cg, tot[0]);
-    else if (MODE == P5_CGF)
-        cg_after_update(cg, tot[0]);
     else
         cg_start(cg, tot[0], tot[1]);
 }

@@ -90,7 +90,10 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
                                  tol_newton=tol_newton, tol_cg=tol_cg)
         slot_info[N] = dict(slots=slots, bytes_per_slot=per)
     if sessions_per_N is None:
-        sessions_per_N = {N: min(2 * slot_info[N]["slots"], 64) for N in Ns}
+        # the workload's session pool: 16 RVEs per grid size, each following
+        # its own strain path, so the work per request (elastic at first,
+        # plastic after a few increments) does not depend on the memory
+        sessions_per_N = {N: 16 for N in Ns}
     # sessions and microstructures are made before the clock starts
     sess = {}
     sid = 0
@@ -195,8 +198,10 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
     per_N = {}
     for N in Ns:
         l = np.array([r["t_done"] - r["t_submit"] for r in results if sess[r["session_id"]][0] == N]) * 1e3
+        cgs = [r["cg_iters"] for r in results if sess[r["session_id"]][0] == N]
         per_N[N] = dict(count=int(l.size), p50_ms=float(np.percentile(l, 50)) if l.size else None,
                         p99_ms=float(np.percentile(l, 99)) if l.size else None,
+                        mean_cg_iters=float(np.mean(cgs)) if cgs else None,
                         slots=slot_info[N]["slots"], sessions=sessions_per_N[N],
                         evictions=infos[N]["evictions"], max_concurrent=infos[N]["max_concurrent"],
                         mean_batch=round(infos[N]["mean_batch"], 2))

@@ -70,3 +70,15 @@ def test_cg_roofline_from_kernel_times():
         assert abs(rf["kernels"][k]["GB/s"] - b[k + "_f32"] * V / 1e-3 / 1e9) < 0.1
     assert rf["matvec"]["ms_per_field_iter"] == 5.0 and rf["iteration"]["ms_per_field_iter"] == 6.0
     assert abs(rf["iteration"]["bytes_per_voxel"] - 460.8) < 0.2
+
+
+def test_cg_roofline_of_the_fused_iteration():
+    # the mixed path: P1 (with <p, C:p>), P2-P4, P5 (r update), cg_rr; the
+    # iteration moves 388.8 B/voxel at 243^3 and the matvec is P1-P5
+    eff = {"p1_cgf": 100, "p5_cgf": 100, "cg_rr": 100, "p2": 117, "p3": 117, "p4": 117}
+    prof = {k + "_f32": (float(n), n) for k, n in eff.items()}
+    rf = bench.cg_roofline(prof, 243, 100, 5, 1, "_f32", hbm=1000.0)
+    assert set(rf["kernels"]) == set(eff)
+    assert rf["matvec"]["ms_per_field_iter"] == 5.0 and rf["iteration"]["ms_per_field_iter"] == 6.0
+    assert abs(rf["iteration"]["bytes_per_voxel"] - 388.8) < 0.2
+    assert rf["matvec"]["bytes_per_voxel"] == rf["iteration"]["bytes_per_voxel"]
