@@ -546,6 +546,39 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
 // six components split over a lane pair duplicated n . tau n and needed
 // shuffles (at 243^3 the separate phase took P3 from 0.206 to 0.185 ms in
 // FP32 and from 7.4 to 6.2 ms in FP64).
+//
+// The middle of a tile (W columns of one x2 frequency, all six components,
+// after stage A): stage B forward in place (permuted order), Ghat, stage B
+// inverse in place; the caller synchronises before and after.
+template <int N, int N1, int W, int NT, typename T>
+__device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, int col0, int k2g, T scale,
+                                               int tid) {
+    constexpr int H = (N + 1) / 2, N2 = N / N1, P = 6 * W;
+    const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
+    if (N2 > 1) {
+        for (int it = tid; it < P * N1; it += NT) {
+            const int pc = it % P, k1 = it / P;
+            const int c = pc / W, w = pc - c * W;
+            if (col0 + w < H) fwdB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+        }
+        __syncthreads();
+    }
+    for (int it = tid; it < W * N; it += NT) {
+        const int w = it % W, pos = it / W, col = col0 + w;
+        const int k1 = pos / N2, k2 = pos - k1 * N2;
+        const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
+        if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
+    }
+    __syncthreads();
+    if (N2 > 1) {
+        for (int it = tid; it < P * N1; it += NT) {
+            const int pc = it % P, k1 = it / P;
+            const int c = pc / W, w = pc - c * W;
+            if (col0 + w < H) invB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+        }
+    }
+}
+
 template <int N, typename T, int NA = Plan<N>::N1, int TV = 0>
 __global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T3, (sizeof(T) == 4 && Cfg<N, T, NA, TV>::T3 <= 512)
                                                       ? (Cfg<N, T, NA, TV>::T3 <= 256 ? 4 : 2)
@@ -572,38 +605,91 @@ __global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T3, (sizeof(T) == 4 && Cfg<
         if (col < H) fwdA<N, N1, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
     }
     __syncthreads();
-    const T scale = (T)a.scale;
-    const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
-    // Separate middle phases: stage B forward in place (permuted order),
-    // Ghat with one thread per (column, frequency) holding all six
-    // components, stage B inverse in place.
-    if (N2 > 1) {
-        for (int it = tid; it < P * N1; it += NT) {
-            const int pc = it % P, k1 = it / P;
-            const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) fwdB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
-        }
-        __syncthreads();
-    }
-    for (int it = tid; it < W * N; it += NT) {
-        const int w = it % W, pos = it / W, col = col0 + w;
-        const int k1 = pos / N2, k2 = pos - k1 * N2;
-        const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
-        if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
-    }
-    __syncthreads();
-    if (N2 > 1) {
-        for (int it = tid; it < P * N1; it += NT) {
-            const int pc = it % P, k1 = it / P;
-            const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) invB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
-        }
-    }
+    p3_tile_middle<N, N1, W, NT, T>(buf, tw, col0, k2g, (T)a.scale, tid);
     __syncthreads();
     for (int it = tid; it < P * N2; it += NT) {
         const int pc = it % P, t = it / P;
         const int c = pc / W, w = pc - c * W, col = col0 + w;
         if (col < H) invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, t, tw);
+    }
+}
+
+// P3 with the next tile's loads in flight (FP32): a persistent grid whose
+// blocks take tiles (W columns of one x2 frequency of one field) in turn,
+// with two tile buffers in shared memory. The loads of tile i+1 are issued
+// as asynchronous 8-byte copies (cp.async) before tile i is transformed,
+// so the loads overlap the transforms instead of alternating with them.
+// Stage A forward then runs in place in shared memory; the rest is k_p3's.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int N, int NA, int TV>
+__global__ void __launch_bounds__(Cfg<N, float, NA, TV>::T3, 1) k_p3_pipe(PassArgs a, int nfields) {
+    using T = float;
+    using C = Cfg<N, T, NA, TV>;
+    constexpr int H = C::H, W = C::W3, NT = C::T3;
+    constexpr int N1 = NA, N2 = N / NA;
+    constexpr int NCB = (H + W - 1) / W;  // column blocks per x2 frequency
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* const buf0 = tw + N;             // two tiles, [6][N][W] each
+    cplx<T>* const buf1 = buf0 + 6 * N * W;
+    const int tid = threadIdx.x;
+    load_tw<T>(tw, a.tw, N);
+    const long long NH = (long long)N * H;
+    const int ntiles = NCB * N * nfields;
+    auto tile_on = [&](int t, int& f, int& k2g, int& col0) {
+        f = t / (NCB * N);
+        const int r = t - f * NCB * N;
+        k2g = r / NCB;
+        col0 = (r - k2g * NCB) * W;
+        return !(a.active && !a.active[f]) && !(a.cg && a.cg[f].done);
+    };
+    // asynchronous copies of one tile into buf (columns past H are skipped)
+    auto issue = [&](int t, cplx<T>* buf) {
+        int f, k2g, col0;
+        if (t >= ntiles || !tile_on(t, f, k2g, col0)) return;
+        const cplx<T>* sp = (const cplx<T>*)a.out + f * a.sstride;
+        for (int it = tid; it < 6 * N * W; it += NT) {
+            const int w = it % W, cx = it / W;  // cx = c * N + x1
+            if (col0 + w < H) {
+                const int c = cx / N, x1 = cx - c * N;
+                cp_async8(buf + cx * W + w, sp + c * N * NH + (long long)x1 * NH + k2g * H + col0 + w);
+            }
+        }
+    };
+    issue(blockIdx.x, buf0);
+    cp_async_commit();
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        issue(t + gridDim.x, (i & 1) ? buf0 : buf1);
+        cp_async_commit();
+        cp_async_wait1();  // this thread's copies of tile t have landed
+        __syncthreads();   // ... and every thread's
+        int f, k2g, col0;
+        if (tile_on(t, f, k2g, col0)) {
+            cplx<T>* buf = (i & 1) ? buf1 : buf0;
+            constexpr int P = 6 * W;
+            for (int it = tid; it < P * N2; it += NT) {
+                const int pc = it % P, tt = it / P;
+                const int c = pc / W, w = pc - c * W;
+                if (col0 + w < H) fwdA<N, N1, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, tt, tw);
+            }
+            __syncthreads();
+            p3_tile_middle<N, N1, W, NT, T>(buf, tw, col0, k2g, (T)a.scale, tid);
+            __syncthreads();
+            cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
+            for (int it = tid; it < P * N2; it += NT) {
+                const int pc = it % P, tt = it / P;
+                const int c = pc / W, w = pc - c * W, col = col0 + w;
+                if (col < H) invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, tt, tw);
+            }
+        }
+        __syncthreads();  // the buffer is refilled two tiles later
     }
 }
 
