@@ -550,9 +550,13 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
 // The middle of a tile (W columns of one x2 frequency, all six components,
 // after stage A): stage B forward in place (permuted order), Ghat, stage B
 // inverse in place; the caller synchronises before and after.
-template <int N, int N1, int W, int NT, typename T>
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+template <int N, int N1, int W, int NT, typename T, typename Sync = BlockSync>
 __device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, int col0, int k2g, T scale,
-                                               int tid) {
+                                               int tid, Sync sync = Sync{}) {
     constexpr int H = (N + 1) / 2, N2 = N / N1, P = 6 * W;
     const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
     if (N2 > 1) {
@@ -561,7 +565,7 @@ __device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, 
             const int c = pc / W, w = pc - c * W;
             if (col0 + w < H) fwdB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
         }
-        __syncthreads();
+        sync();
     }
     for (int it = tid; it < W * N; it += NT) {
         const int w = it % W, pos = it / W, col = col0 + w;
@@ -569,7 +573,7 @@ __device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, 
         const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
         if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
     }
-    __syncthreads();
+    sync();
     if (N2 > 1) {
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
@@ -614,82 +618,108 @@ __global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T3, (sizeof(T) == 4 && Cfg<
     }
 }
 
-// P3 with the next tile's loads in flight (FP32): a persistent grid whose
-// blocks take tiles (W columns of one x2 frequency of one field) in turn,
-// with two tile buffers in shared memory. The loads of tile i+1 are issued
-// as asynchronous 8-byte copies (cp.async) before tile i is transformed,
-// so the loads overlap the transforms instead of alternating with them.
-// Stage A forward then runs in place in shared memory; the rest is k_p3's.
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+// P3 with its warps split into two roles (FP32), so that global loads,
+// transforms and global stores of different tiles overlap within one block.
+// A persistent grid; a block takes tiles (W columns of one x2 frequency of
+// one field) in turn through two tile buffers in shared memory:
+//   producer warps  [0, X):      tile j: global -> stage A forward -> buffer j % 2
+//   consumer warps  [X, X + Y):  tile j: stage B, Ghat, stage B inverse in the
+//                                buffer, stage A inverse -> global
+// While the consumers transform tile j, the producers load and transform
+// tile j + 1 into the other buffer. The hand-over uses hardware named
+// barriers (no spin-waits): FULL[b] (producers arrive, consumers wait) and
+// EMPTY[b] (consumers arrive once they are done with buffer b, producers
+// wait before refilling it for tile j + 2); the consumers' own phases
+// synchronise on a third barrier among them only. Each role runs the same
+// sequence of tiles with uniform control flow, so every barrier generation
+// gets exactly X + Y (or Y) arrivals.
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
 
-template <int N, int NA, int TV>
-__global__ void __launch_bounds__(Cfg<N, float, NA, TV>::T3, 1) k_p3_pipe(PassArgs a, int nfields) {
+enum : int { P3WS_BAR_CONS = 1, P3WS_BAR_FULL = 2, P3WS_BAR_EMPTY = 4 };
+
+template <int N, int NA, int XR = 2, int NTMAX = 896>
+struct P3ws {
+    using C = Cfg<N, float, NA, 0>;
+    static constexpr int W = C::W3, N1 = NA, N2 = N / NA;
+    static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
+    // producers: stage A items (6 W N2 pencils of N1 points) in XR rounds;
+    // consumers: stage B items (6 W N1) in two rounds, within NTMAX threads
+    // in all (896: 72 registers each)
+    static constexpr int X = rup32((6 * W * N2 + XR - 1) / XR);
+    static constexpr int Y0 = rup32((6 * W * N1 + 1) / 2);
+    static constexpr int Y = Y0 > NTMAX - X ? NTMAX - X : Y0;
+    static constexpr int NT = X + Y;
+    static constexpr size_t smem = (size_t)(N + 2 * 6 * N * W) * sizeof(cplx<float>);
+    static_assert(X >= 32 && Y >= 32 && NT <= 1024, "P3 roles");
+};
+
+struct ConsumerSync {
+    int n;
+    __device__ __forceinline__ void operator()() const { named_sync(P3WS_BAR_CONS, n); }
+};
+
+template <int N, int NA, int XR = 2, int NTMAX = 896>
+__global__ void __launch_bounds__(P3ws<N, NA, XR, NTMAX>::NT, 1) k_p3_ws(PassArgs a, int nfields) {
     using T = float;
-    using C = Cfg<N, T, NA, TV>;
-    constexpr int H = C::H, W = C::W3, NT = C::T3;
-    constexpr int N1 = NA, N2 = N / NA;
+    using S = P3ws<N, NA, XR, NTMAX>;
+    constexpr int H = (N + 1) / 2, W = S::W, N1 = NA, N2 = N / NA, X = S::X, Y = S::Y, NT = S::NT;
     constexpr int NCB = (H + W - 1) / W;  // column blocks per x2 frequency
+    constexpr int P = 6 * W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* const buf0 = tw + N;             // two tiles, [6][N][W] each
+    cplx<T>* const buf0 = tw + N;  // two tiles, [6][N][W] each
     cplx<T>* const buf1 = buf0 + 6 * N * W;
-    const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
+    __syncthreads();
     const long long NH = (long long)N * H;
     const int ntiles = NCB * N * nfields;
-    auto tile_on = [&](int t, int& f, int& k2g, int& col0) {
-        f = t / (NCB * N);
+    const int J = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const bool producer = threadIdx.x < X;
+    for (int j = 0; j < J; ++j) {
+        const int t = blockIdx.x + j * gridDim.x;
+        const int b = j & 1;
+        cplx<T>* const buf = b ? buf1 : buf0;
+        const int f = t / (NCB * N);
         const int r = t - f * NCB * N;
-        k2g = r / NCB;
-        col0 = (r - k2g * NCB) * W;
-        return !(a.active && !a.active[f]) && !(a.cg && a.cg[f].done);
-    };
-    // asynchronous copies of one tile into buf (columns past H are skipped)
-    auto issue = [&](int t, cplx<T>* buf) {
-        int f, k2g, col0;
-        if (t >= ntiles || !tile_on(t, f, k2g, col0)) return;
-        const cplx<T>* sp = (const cplx<T>*)a.out + f * a.sstride;
-        for (int it = tid; it < 6 * N * W; it += NT) {
-            const int w = it % W, cx = it / W;  // cx = c * N + x1
-            if (col0 + w < H) {
-                const int c = cx / N, x1 = cx - c * N;
-                cp_async8(buf + cx * W + w, sp + c * N * NH + (long long)x1 * NH + k2g * H + col0 + w);
+        const int k2g = r / NCB;
+        const int col0 = (r - k2g * NCB) * W;
+        const bool live = !(a.active && !a.active[f]) && !(a.cg && a.cg[f].done);
+        cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
+        if (producer) {
+            if (j >= 2) named_sync(P3WS_BAR_EMPTY + b, NT);
+            if (live) {
+                for (int it = threadIdx.x; it < P * N2; it += X) {
+                    const int pc = it % P, tt = it / P;
+                    const int c = pc / W, w = pc - c * W, col = col0 + w;
+                    if (col < H)
+                        fwdA<N, N1, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, tt, tw);
+                }
+            }
+            __threadfence_block();
+            named_arrive(P3WS_BAR_FULL + b, NT);
+        } else {
+            const int tid = threadIdx.x - X;
+            named_sync(P3WS_BAR_FULL + b, NT);
+            if (live) {
+                p3_tile_middle<N, N1, W, Y, T>(buf, tw, col0, k2g, (T)a.scale, tid, ConsumerSync{Y});
+                named_sync(P3WS_BAR_CONS, Y);
+                for (int it = tid; it < P * N2; it += Y) {
+                    const int pc = it % P, tt = it / P;
+                    const int c = pc / W, w = pc - c * W, col = col0 + w;
+                    if (col < H)
+                        invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, tt, tw);
+                }
+            }
+            if (j + 2 < J) {
+                __threadfence_block();
+                named_arrive(P3WS_BAR_EMPTY + b, NT);
             }
         }
-    };
-    issue(blockIdx.x, buf0);
-    cp_async_commit();
-    int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        issue(t + gridDim.x, (i & 1) ? buf0 : buf1);
-        cp_async_commit();
-        cp_async_wait1();  // this thread's copies of tile t have landed
-        __syncthreads();   // ... and every thread's
-        int f, k2g, col0;
-        if (tile_on(t, f, k2g, col0)) {
-            cplx<T>* buf = (i & 1) ? buf1 : buf0;
-            constexpr int P = 6 * W;
-            for (int it = tid; it < P * N2; it += NT) {
-                const int pc = it % P, tt = it / P;
-                const int c = pc / W, w = pc - c * W;
-                if (col0 + w < H) fwdA<N, N1, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, tt, tw);
-            }
-            __syncthreads();
-            p3_tile_middle<N, N1, W, NT, T>(buf, tw, col0, k2g, (T)a.scale, tid);
-            __syncthreads();
-            cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
-            for (int it = tid; it < P * N2; it += NT) {
-                const int pc = it % P, tt = it / P;
-                const int c = pc / W, w = pc - c * W, col = col0 + w;
-                if (col < H) invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, tt, tw);
-            }
-        }
-        __syncthreads();  // the buffer is refilled two tiles later
     }
 }
 
