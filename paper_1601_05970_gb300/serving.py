@@ -90,10 +90,12 @@ def run(rate, duration, Ns=(27, 45, 75, 135), weights=(0.4, 0.3, 0.2, 0.1),
                                  tol_newton=tol_newton, tol_cg=tol_cg)
         slot_info[N] = dict(slots=slots, bytes_per_slot=per)
     if sessions_per_N is None:
-        # the workload's session pool: 16 RVEs per grid size, each following
-        # its own strain path, so the work per request (elastic at first,
-        # plastic after a few increments) does not depend on the memory
-        sessions_per_N = {N: 16 for N in Ns}
+        # the workload's session pool: 64 RVEs (Gauss points) per grid size,
+        # each following its own strain path, so the work per request
+        # (elastic at first, plastic after a few increments) does not depend
+        # on the memory. A session's increments run one after another, so
+        # the pool also bounds the requests of a size in flight at once.
+        sessions_per_N = {N: 64 for N in Ns}
     # sessions and microstructures are made before the clock starts
     sess = {}
     sid = 0
