@@ -144,7 +144,7 @@ def flops_per_voxel(N):
 KERNEL_FILES = ("common.cuh", "fft_core.cuh", "passes.cuh")
 FS_KERNEL_FILES = KERNEL_FILES + ("fs_passes.cuh",)
 TRAFFIC = {"p1_cgf_f32": {"N": 243, "bytes": 2413.6e6, "digest": "6796302d3e5845c1", "files": KERNEL_FILES},
-           "fs_p1_cg_f32": {"N": 243, "bytes": 3579.6e6, "digest": "23608171e96a0ffe", "files": FS_KERNEL_FILES}}
+           "fs_p1_cgf_f32": {"N": 243, "bytes": 3587.2e6, "digest": "03d3c599251d8084", "files": FS_KERNEL_FILES}}
 
 
 def _strip_comments(src: bytes) -> bytes:
@@ -195,6 +195,9 @@ def parse():
                     help="enqueue CG iterations from the host instead of the graph loop")
     ap.add_argument("--no-tune", action="store_true",
                     help="run the default schedules of the FP32 passes (no autotuning)")
+    ap.add_argument("--projection-only", action="store_true",
+                    help="time the FP32 projection G tau of a random field on a bare cell of "
+                         "grid --N (the five passes alone, default schedules) and print it")
     ap.add_argument("--finite-strain-only", action="store_true",
                     help="run only the finite-strain line (mixed, --N 243 or 135) and print it")
     ap.add_argument("--serve-rates", default="50,100,200,500",
@@ -555,6 +558,35 @@ def fs_bytes_per_voxel(N):
             "fs_cg_rr_f32": 0.0}
 
 
+def projection_line(N, steps, warmup):
+    """G tau of a random FP32 field on a bare mixed cell of grid N (one
+    phase, no tangent RHS: a small device footprint), the five passes with
+    their default schedules: ms per projection between CUDA events on the
+    cell's stream, and the library's per-kernel times."""
+    import torch
+    cell = fftg.Cell(N, np.zeros((N, N, N), dtype=np.int8), I.TWO_PHASE, precision="mixed", nrhs_tangent=0)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(N)
+    tau = torch.randn(6 * N ** 3, device="cuda", generator=gen)
+    out = torch.empty_like(tau)
+    with torch.cuda.stream(cell.stream):
+        for _ in range(max(1, warmup)):
+            cell.project(tau, out)
+        cell.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cell.stream)
+        for _ in range(steps):
+            cell.project(tau, out)
+        e1.record(cell.stream)
+        e1.synchronize()
+    prof = cell.profile_read()
+    cell.profile(False)
+    cell.close()
+    return {"what": "FP32 projection G tau, five passes (P1 plain, P2, P3, P4, P5 plain), default schedules",
+            "N": N, "projections": steps, "ms_per_projection": e0.elapsed_time(e1) / max(1, steps),
+            "kernels": {k: {"ms_per_launch": ms / max(1, n), "launches": n} for k, (ms, n) in prof.items()}}
+
+
 def finite_strain_line(N=243, warm=1, timed=2):
     """The finite-strain extension (St. Venant-Kirchhoff, first
     Piola-Kirchhoff stress, gradient projection) on the N^3 spheres cell
@@ -748,6 +780,10 @@ def main():
     if args.finite_strain_only:
         if rank == 0:
             print(json.dumps(finite_strain_line(args.N)))
+        return 0
+    if args.projection_only:
+        if rank == 0:
+            print(json.dumps(projection_line(args.N, args.steps, args.warmup)))
         return 0
 
     N = args.N
