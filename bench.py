@@ -564,6 +564,8 @@ def projection_line(N, steps, warmup):
     their default schedules: ms per projection between CUDA events on the
     cell's stream, and the library's per-kernel times."""
     import torch
+    from paper_1601_05970_gb300 import fftg
+    from paper_1601_05970_gb300 import inputs as I
     cell = fftg.Cell(N, np.zeros((N, N, N), dtype=np.int8), I.TWO_PHASE, precision="mixed", nrhs_tangent=0)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(N)
