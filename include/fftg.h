@@ -398,8 +398,8 @@ long long fftg_launch_count(const fftg_handle* h);
  * schedules per grid size and pass: the radix split of the pencil transform
  * (the default split or the other one, e.g. 27 x 9 or 9 x 27 at N = 243)
  * and the tile (rows per block of P1/P5, columns per block of P2-P4; for
- * P3 also a persistent grid whose producer warps load and transform the
- * next tile while its consumer warps finish the current one).
+ * P3 also the default tile with stage B, Ghat and the inverse stage B in one
+ * phase).
  * Every schedule computes the same transforms (results agree to FP32
  * rounding). The choice is process-wide per grid size and applies to
  * launches enqueued afterwards; a handle's CUDA graphs keep the kernels they

@@ -550,13 +550,9 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
 // The middle of a tile (W columns of one x2 frequency, all six components,
 // after stage A): stage B forward in place (permuted order), Ghat, stage B
 // inverse in place; the caller synchronises before and after.
-struct BlockSync {
-    __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
-
-template <int N, int N1, int W, int NT, typename T, typename Sync = BlockSync>
+template <int N, int N1, int W, int NT, typename T>
 __device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, int col0, int k2g, T scale,
-                                               int tid, Sync sync = Sync{}) {
+                                               int tid) {
     constexpr int H = (N + 1) / 2, N2 = N / N1, P = 6 * W;
     const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
     if (N2 > 1) {
@@ -565,7 +561,7 @@ __device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, 
             const int c = pc / W, w = pc - c * W;
             if (col0 + w < H) fwdB<N, N1, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
         }
-        sync();
+        __syncthreads();
     }
     for (int it = tid; it < W * N; it += NT) {
         const int w = it % W, pos = it / W, col = col0 + w;
@@ -573,7 +569,7 @@ __device__ __forceinline__ void p3_tile_middle(cplx<T>* buf, const cplx<T>* tw, 
         const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
         if (col < H) ghat_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
     }
-    sync();
+    __syncthreads();
     if (N2 > 1) {
         for (int it = tid; it < P * N1; it += NT) {
             const int pc = it % P, k1 = it / P;
@@ -618,108 +614,129 @@ __global__ void __launch_bounds__(Cfg<N, T, NA, TV>::T3, (sizeof(T) == 4 && Cfg<
     }
 }
 
-// P3 with its warps split into two roles (FP32), so that global loads,
-// transforms and global stores of different tiles overlap within one block.
-// A persistent grid; a block takes tiles (W columns of one x2 frequency of
-// one field) in turn through two tile buffers in shared memory:
-//   producer warps  [0, X):      tile j: global -> stage A forward -> buffer j % 2
-//   consumer warps  [X, X + Y):  tile j: stage B, Ghat, stage B inverse in the
-//                                buffer, stage A inverse -> global
-// While the consumers transform tile j, the producers load and transform
-// tile j + 1 into the other buffer. The hand-over uses hardware named
-// barriers (no spin-waits): FULL[b] (producers arrive, consumers wait) and
-// EMPTY[b] (consumers arrive once they are done with buffer b, producers
-// wait before refilling it for tile j + 2); the consumers' own phases
-// synchronise on a third barrier among them only. Each role runs the same
-// sequence of tiles with uniform control flow, so every barrier generation
-// gets exactly X + Y (or Y) arrivals.
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void named_arrive(int id, int nthreads) {
-    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-enum : int { P3WS_BAR_CONS = 1, P3WS_BAR_FULL = 2, P3WS_BAR_EMPTY = 4 };
-
-template <int N, int NA, int XR = 2, int NTMAX = 896>
-struct P3ws {
+// P3 with stage B, Ghat and the inverse stage B in one phase (FP32, two-stage
+// splits with N2 <= 9). One thread per (column, k1) streams the six
+// components through its N2-point forward DFT and accumulates, for its N2
+// frequencies kk = k1 + N1 k2, only t = tau n: the closed form of Ghat
+// (Appendix A) needs tau through t alone, as n(x)u + u(x)n with
+// u = t - (n.t / 2) n. Each output component is then formed from n and u,
+// taken through the inverse N2-point DFT with its twiddles, and stored back
+// in place. Against the default tile this passes each point through shared
+// memory twice instead of five times and needs two barriers instead of
+// four, at up to 128 registers per thread (blocks of at most 256 threads,
+// two per SM). The results agree with the default's to FP32 rounding (t is
+// summed in another order).
+template <int N, int NA>
+struct P3f {
     using C = Cfg<N, float, NA, 0>;
     static constexpr int W = C::W3, N1 = NA, N2 = N / NA;
+    static constexpr bool ok = N2 > 1 && N2 <= 9;
     static constexpr int rup32(int x) { return ((x + 31) / 32) * 32; }
-    // producers: stage A items (6 W N2 pencils of N1 points) in XR rounds;
-    // consumers: stage B items (6 W N1) in two rounds, within NTMAX threads
-    // in all (896: 72 registers each)
-    static constexpr int X = rup32((6 * W * N2 + XR - 1) / XR);
-    static constexpr int Y0 = rup32((6 * W * N1 + 1) / 2);
-    static constexpr int Y = Y0 > NTMAX - X ? NTMAX - X : Y0;
-    static constexpr int NT = X + Y;
-    static constexpr size_t smem = (size_t)(N + 2 * 6 * N * W) * sizeof(cplx<float>);
-    static_assert(X >= 32 && Y >= 32 && NT <= 1024, "P3 roles");
+    // stage-A items in two rounds and one thread per fused item, within 256
+    // threads (two blocks per SM at up to 128 registers each)
+    static constexpr int TA0 = rup32((6 * W * N2 + 1) / 2), TB0 = rup32(W * N1);
+    static constexpr int TA = TA0 > 256 ? 256 : TA0, TB = TB0 > 256 ? 256 : TB0;
+    static constexpr int NT = TA > TB ? TA : TB;
 };
 
-struct ConsumerSync {
-    int n;
-    __device__ __forceinline__ void operator()() const { named_sync(P3WS_BAR_CONS, n); }
-};
-
-template <int N, int NA, int XR = 2, int NTMAX = 896>
-__global__ void __launch_bounds__(P3ws<N, NA, XR, NTMAX>::NT, 1) k_p3_ws(PassArgs a, int nfields) {
+template <int N, int NA>
+__global__ void __launch_bounds__(P3f<N, NA>::NT, 2) k_p3f(PassArgs a) {
     using T = float;
-    using S = P3ws<N, NA, XR, NTMAX>;
-    constexpr int H = (N + 1) / 2, W = S::W, N1 = NA, N2 = N / NA, X = S::X, Y = S::Y, NT = S::NT;
-    constexpr int NCB = (H + W - 1) / W;  // column blocks per x2 frequency
-    constexpr int P = 6 * W;
+    using S = P3f<N, NA>;
+    static_assert(S::ok, "fused P3 needs a two-stage split with N2 <= 9");
+    constexpr int H = (N + 1) / 2, W = S::W, N1 = NA, N2 = N / NA, NT = S::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* const buf0 = tw + N;  // two tiles, [6][N][W] each
-    cplx<T>* const buf1 = buf0 + 6 * N * W;
+    cplx<T>* buf = tw + N;  // [6][N][W]
+    const int f = blockIdx.z;
+    if (a.active && !a.active[f]) return;
+    if (a.cg && a.cg[f].done) return;
+    const int tid = threadIdx.x;
     load_tw<T>(tw, a.tw, N);
     __syncthreads();
+    const int col0 = blockIdx.x * W, k2g = blockIdx.y;
+    cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
+    constexpr int P = 6 * W;
     const long long NH = (long long)N * H;
-    const int ntiles = NCB * N * nfields;
-    const int J = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const bool producer = threadIdx.x < X;
-    for (int j = 0; j < J; ++j) {
-        const int t = blockIdx.x + j * gridDim.x;
-        const int b = j & 1;
-        cplx<T>* const buf = b ? buf1 : buf0;
-        const int f = t / (NCB * N);
-        const int r = t - f * NCB * N;
-        const int k2g = r / NCB;
-        const int col0 = (r - k2g * NCB) * W;
-        const bool live = !(a.active && !a.active[f]) && !(a.cg && a.cg[f].done);
-        cplx<T>* sp = (cplx<T>*)a.out + f * a.sstride;
-        if (producer) {
-            if (j >= 2) named_sync(P3WS_BAR_EMPTY + b, NT);
-            if (live) {
-                for (int it = threadIdx.x; it < P * N2; it += X) {
-                    const int pc = it % P, tt = it / P;
-                    const int c = pc / W, w = pc - c * W, col = col0 + w;
-                    if (col < H)
-                        fwdA<N, N1, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, tt, tw);
+    for (int it = tid; it < P * N2; it += NT) {
+        const int pc = it % P, t = it / P;
+        const int c = pc / W, w = pc - c * W, col = col0 + w;
+        if (col < H) fwdA<N, N1, T>(sp + c * N * NH + k2g * H + col, (int)NH, buf + c * N * W + w, W, t, tw);
+    }
+    __syncthreads();
+    const T scale = (T)a.scale;
+    const T f2 = (T)((k2g <= (N - 1) / 2) ? k2g : k2g - N);
+    for (int it = tid; it < W * N1; it += NT) {
+        const int w = it % W, k1 = it / W, col = col0 + w;
+        if (col >= H) continue;
+        cplx<T>* base = buf + (N2 * k1) * W + w;  // position N2*k1 + q at base[q * W]
+        T n[N2][3];
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const int kk = k1 + N1 * k2;
+            const T f1 = (T)((kk <= (N - 1) / 2) ? kk : kk - N), f3 = (T)col;
+            const T q2 = f1 * f1 + f2 * f2 + f3 * f3;
+            const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
+            n[k2][0] = f1 * inv;
+            n[k2][1] = f2 * inv;
+            n[k2][2] = f3 * inv;
+        }
+        cplx<T> t[N2][3];
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) t[k2][0] = t[k2][1] = t[k2][2] = mk(T(0), T(0));
+        // t = tau n over the components (11, 22, 33, 23, 13, 12)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            cplx<T> v[N2];
+#pragma unroll
+            for (int q = 0; q < N2; ++q) v[q] = base[c * N * W + q * W];
+            RegDFT<N, N2, -1, T>::run(v, tw);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                if (c < 3) {
+                    t[k2][c] = t[k2][c] + n[k2][c] * v[k2];
+                } else {
+                    // off-diagonal (i, j): 23 -> (1, 2), 13 -> (0, 2), 12 -> (0, 1)
+                    const int i = c == 3 ? 1 : 0, j = c == 5 ? 1 : 2;
+                    t[k2][i] = t[k2][i] + n[k2][j] * v[k2];
+                    t[k2][j] = t[k2][j] + n[k2][i] * v[k2];
                 }
-            }
-            __threadfence_block();
-            named_arrive(P3WS_BAR_FULL + b, NT);
-        } else {
-            const int tid = threadIdx.x - X;
-            named_sync(P3WS_BAR_FULL + b, NT);
-            if (live) {
-                p3_tile_middle<N, N1, W, Y, T>(buf, tw, col0, k2g, (T)a.scale, tid, ConsumerSync{Y});
-                named_sync(P3WS_BAR_CONS, Y);
-                for (int it = tid; it < P * N2; it += Y) {
-                    const int pc = it % P, tt = it / P;
-                    const int c = pc / W, w = pc - c * W, col = col0 + w;
-                    if (col < H)
-                        invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, tt, tw);
-                }
-            }
-            if (j + 2 < J) {
-                __threadfence_block();
-                named_arrive(P3WS_BAR_EMPTY + b, NT);
             }
         }
+        // u = t - (n.t / 2) n, in place
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const cplx<T> h = T(-0.5) * (n[k2][0] * t[k2][0] + n[k2][1] * t[k2][1] + n[k2][2] * t[k2][2]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) t[k2][i] = t[k2][i] + n[k2][i] * h;
+        }
+        // each output component: scale (n(x)u + u(x)n), inverse DFT, twiddle, store
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            cplx<T> v[N2];
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                if (c < 3) {
+                    v[k2] = (T(2) * scale * n[k2][c]) * t[k2][c];
+                } else {
+                    const int i = c == 3 ? 1 : 0, j = c == 5 ? 1 : 2;
+                    v[k2] = (scale * n[k2][i]) * t[k2][j] + (scale * n[k2][j]) * t[k2][i];
+                }
+            }
+            RegDFT<N, N2, +1, T>::run(v, tw);
+#pragma unroll
+            for (int q = 0; q < N2; ++q) {
+                cplx<T> z = v[q];
+                if (k1 > 0 && q > 0) z = twmul<+1>(z, tw[q * k1]);  // q*k1 < N
+                base[c * N * W + q * W] = z;
+            }
+        }
+    }
+    __syncthreads();
+    for (int it = tid; it < P * N2; it += NT) {
+        const int pc = it % P, t = it / P;
+        const int c = pc / W, w = pc - c * W, col = col0 + w;
+        if (col < H) invA<N, N1, T>(buf + c * N * W + w, W, sp + c * N * NH + k2g * H + col, (int)NH, t, tw);
     }
 }
 

@@ -10,11 +10,10 @@
 //                                 2 32 columns per block; 3 both
 //   P3 (x1 + Ghat, columns):      0 default; 1 the other radix split;
 //                                 2 half the columns per block;
-//                                 3 the default tile in a persistent grid
-//                                   with producer and consumer warps
-//                                   (k_p3_ws): the next tile is loaded and
-//                                   transformed along x1 while the current
-//                                   one finishes
+//                                 3 the default tile with stage B, Ghat
+//                                   and the inverse stage B in one phase
+//                                   (k_p3f; splits with 1 < N2 <= 9, else
+//                                   the default)
 //
 // A schedule changes only how the same transforms are split into register
 // DFTs and how pencils are grouped into blocks: the results agree to FP32
@@ -45,29 +44,10 @@ struct AltSplit {
 template <int N, int TK, int V>
 struct VariantOf {
     static constexpr bool cols = TK == TK_P2 || TK == TK_P4;
-    static constexpr bool ws = TK == TK_P3 && V == 3;
+    static constexpr bool fused = TK == TK_P3 && V == 3;
     static constexpr int A = (V == 1 || (V == 3 && cols)) ? AltSplit<N>::A : Plan<N>::N1;
-    static constexpr int TV = V == 0 ? 0 : V == 1 ? 0 : V == 2 ? 1 : cols ? 1 : ws ? 0 : 2;
+    static constexpr int TV = V == 0 ? 0 : V == 1 ? 0 : V == 2 ? 1 : cols ? 1 : fused ? 0 : 2;
 };
-
-// Blocks of the persistent P3: as many as are resident at once, at most
-// one per tile.
-template <int N, int NA>
-cudaError_t launch_p3_ws(const PassArgs& a, int nf, cudaStream_t s) {
-    using S = P3ws<N, NA>;
-    using C = Cfg<N, float, NA, 0>;
-    const int ntiles = ((C::H + S::W - 1) / S::W) * N * nf;
-    cudaError_t e = cudaFuncSetAttribute(k_p3_ws<N, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p3_ws<N, NA>, S::NT, S::smem)) != cudaSuccess)
-        return e;
-    const int blocks = std::min(ntiles, std::max(1, per_sm) * sms);
-    k_p3_ws<N, NA><<<blocks, S::NT, S::smem, s>>>(a, nf);
-    return cudaGetLastError();
-}
 
 template <int N, int TK, int V>
 cudaError_t launch_variant(const PassArgs& a, int nf, cudaStream_t s) {
@@ -78,8 +58,9 @@ cudaError_t launch_variant(const PassArgs& a, int nf, cudaStream_t s) {
     } else if constexpr (TK == TK_P5) {
         return launch_k(k_p5<N, float, P5_CGF, float, VO::A, VO::TV>, dim3(C::row_blocks, 1, nf), C::smem_rows,
                         a, s);
-    } else if constexpr (TK == TK_P3 && VO::ws) {
-        return launch_p3_ws<N, VO::A>(a, nf, s);
+    } else if constexpr (TK == TK_P3 && VO::fused && P3f<N, VO::A>::ok) {
+        return launch_k(k_p3f<N, VO::A>, dim3((C::H + C::W3 - 1) / C::W3, N, nf), C::smem_p3, a, s,
+                        P3f<N, VO::A>::NT);
     } else if constexpr (TK == TK_P3) {
         return launch_k(k_p3<N, float, VO::A, VO::TV>, dim3((C::H + C::W3 - 1) / C::W3, N, nf), C::smem_p3, a, s,
                         C::T3);

@@ -74,8 +74,8 @@ def test_every_schedule_matches_the_oracle(N, kind):
 
 def test_schedule_shapes_are_distinct_where_the_grid_allows():
     # 243 = 27 x 9: the other split is 9 x 27; P3's tile halves (variant 2)
-    # or stays the default one in the persistent grid of producer and
-    # consumer warps (variant 3)
+    # or stays the default one with stage B, Ghat and the inverse stage B in
+    # one phase (variant 3)
     d0 = fftg.schedule_describe(243, "p3", 0)
     d1 = fftg.schedule_describe(243, "p3", 1)
     assert d0["split"] == (27, 9) and d1["split"] == (9, 27)
@@ -113,11 +113,12 @@ def test_autotune_picks_a_schedule_and_caches_it(tmp_path, monkeypatch):
 
 
 @pytest.mark.parametrize("N", [135, 243])
-def test_persistent_p3_equals_the_default_bit_for_bit(N):
-    """P3 variant 3 (producer and consumer warps over two tile buffers)
-    does the default tile's operations in the same order, so G tau is
-    identical to the last bit at the full grid sizes (the default's G tau
-    is checked against the oracle at these sizes in the full-size tests)."""
+def test_fused_p3_matches_the_default_at_full_size(N):
+    """P3 variant 3 (stage B, Ghat and the inverse stage B in one phase, t =
+    tau n accumulated over the components) sums in another order than the
+    default tile, so G tau agrees with it to FP32 rounding at the full grid
+    sizes (the default's G tau is checked against the oracle at these sizes
+    in the full-size tests)."""
     rng = np.random.default_rng(7 + N)
     ph = np.zeros((N, N, N), dtype=np.int8)
     tau = rng.standard_normal(6 * N ** 3).astype(np.float32)
@@ -125,8 +126,9 @@ def test_persistent_p3_equals_the_default_bit_for_bit(N):
     for v in (0, 3):
         fftg.schedule_set(N, "p3", v)
         cell = fftg.Cell(N, ph, I.TWO_PHASE, precision="mixed", nrhs_tangent=0)
-        out[v] = cell.project(torch.tensor(tau, device="cuda")).cpu().numpy()
+        out[v] = cell.project(torch.tensor(tau, device="cuda")).cpu().numpy().astype(np.float64)
         cell.close()
     fftg.schedule_set(N, "p3", 0)
-    assert np.array_equal(out[0], out[3])
-    assert np.isfinite(out[3]).all() and np.abs(out[3]).max() > 0
+    assert np.isfinite(out[3]).all()
+    assert np.linalg.norm(out[3] - out[0]) <= 1e-6 * np.linalg.norm(out[0])
+    assert np.abs(out[3] - out[0]).max() <= 1e-5 * np.abs(out[0]).max()
