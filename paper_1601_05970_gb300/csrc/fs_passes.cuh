@@ -354,7 +354,8 @@ __device__ __forceinline__ void ghat_fs_point(cplx<T>* b, int cs, int f1, int f2
 // ------------------------------------------------------------- P3 (x1 + Ghat)
 // As the small-strain P3: stage A forward into shared memory, stage B
 // forward in place, Ghat_fs with one thread per (column, frequency), stage B
-// inverse, stage A inverse back to the spectrum.
+// inverse, stage A inverse back to the spectrum; in FP32 with two-stage
+// splits of N2 <= 9 the middle three phases are one (below).
 template <int N, typename T>
 __global__ void __launch_bounds__(FsCfg<N, T>::T3) k_fs_p3(FsArgs a) {
     using C = FsCfg<N, T>;
@@ -379,27 +380,77 @@ __global__ void __launch_bounds__(FsCfg<N, T>::T3) k_fs_p3(FsArgs a) {
     __syncthreads();
     const T scale = (T)a.scale;
     const int f2 = (k2g <= (N - 1) / 2) ? k2g : k2g - N;
-    if (N2 > 1) {
-        for (int it = tid; it < P * N1; it += NT) {
-            const int pc = it % P, k1 = it / P;
-            const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+    if constexpr (std::is_same<T, float>::value && N2 > 1 && N2 <= 9) {
+        // Stage B, Ghat_fs and the inverse stage B in one phase: row i of
+        // Ghat_fs : A is (A_i . n) n, which needs row i's three components
+        // only. One thread per (column, k1, row) takes them through the
+        // forward N2-point DFT, sums t = A_i . n for its N2 frequencies in
+        // Ghat_fs's order, and writes scale n_j t back through the inverse
+        // DFT and its twiddles: two shared-memory passes per point instead
+        // of five, and two barriers fewer.
+        for (int it = tid; it < W * N1 * 3; it += NT) {
+            const int w = it % W, r = it / W;
+            const int k1 = r % N1, row = r / N1, col = col0 + w;
+            if (col >= H) continue;
+            cplx<T>* base = buf + (3 * row * N + N2 * k1) * W + w;  // component 3 row + j at base[j N W]
+            T n[N2][3];
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int kk = k1 + N1 * k2;
+                const T f1 = T((kk <= (N - 1) / 2) ? kk : kk - N), g2 = T(f2), f3 = T(col);
+                const T q2 = f1 * f1 + g2 * g2 + f3 * f3;
+                const T inv = q2 > T(0) ? rsqrt_t(q2) : T(0);
+                n[k2][0] = f1 * inv;
+                n[k2][1] = g2 * inv;
+                n[k2][2] = f3 * inv;
+            }
+            cplx<T> t[N2];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                cplx<T> v[N2];
+#pragma unroll
+                for (int q = 0; q < N2; ++q) v[q] = base[j * N * W + q * W];
+                RegDFT<N, N2, -1, T>::run(v, tw);
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) t[k2] = j == 0 ? n[k2][0] * v[k2] : t[k2] + n[k2][j] * v[k2];
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                cplx<T> v[N2];
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) v[k2] = (scale * n[k2][j]) * t[k2];
+                RegDFT<N, N2, +1, T>::run(v, tw);
+#pragma unroll
+                for (int q = 0; q < N2; ++q) {
+                    cplx<T> z = v[q];
+                    if (k1 > 0 && q > 0) z = twmul<+1>(z, tw[q * k1]);  // q*k1 < N
+                    base[j * N * W + q * W] = z;
+                }
+            }
+        }
+    } else {
+        if (N2 > 1) {
+            for (int it = tid; it < P * N1; it += NT) {
+                const int pc = it % P, k1 = it / P;
+                const int c = pc / W, w = pc - c * W;
+                if (col0 + w < H) fwdB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+            }
+            __syncthreads();
+        }
+        for (int it = tid; it < W * N; it += NT) {
+            const int w = it % W, pos = it / W, col = col0 + w;
+            const int k1 = pos / N2, k2 = pos - k1 * N2;
+            const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
+            if (col < H)
+                ghat_fs_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
         }
         __syncthreads();
-    }
-    for (int it = tid; it < W * N; it += NT) {
-        const int w = it % W, pos = it / W, col = col0 + w;
-        const int k1 = pos / N2, k2 = pos - k1 * N2;
-        const int kk = k1 + N1 * k2;  // frequency held at position N2*k1 + k2
-        if (col < H)
-            ghat_fs_point<T>(buf + pos * W + w, N * W, (kk <= (N - 1) / 2) ? kk : kk - N, f2, col, scale);
-    }
-    __syncthreads();
-    if (N2 > 1) {
-        for (int it = tid; it < P * N1; it += NT) {
-            const int pc = it % P, k1 = it / P;
-            const int c = pc / W, w = pc - c * W;
-            if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+        if (N2 > 1) {
+            for (int it = tid; it < P * N1; it += NT) {
+                const int pc = it % P, k1 = it / P;
+                const int c = pc / W, w = pc - c * W;
+                if (col0 + w < H) invB<N, false, T>(buf + c * N * W + w, W, buf + c * N * W + w, W, k1, tw);
+            }
         }
     }
     __syncthreads();
