@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
         const double m = tr * (1.0 / 3.0);
         double sig[6];
         double g2;
-        double w[6] = {0, 0, 0, 0, 0, 0};
+        TT w[6] = {TT(0), TT(0), TT(0), TT(0), TT(0), TT(0)};  // in the tangent's precision
         double dg = 0.0;
         bool kneg = false;  // N(x)N coefficient of the tangent positive
         if (nle) {
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
             kneg = b > 0.0;
             const double sbN = eeq > 0.0 ? sqrt(fabs(b)) * (2.0 / 3.0) / eeq : 0.0;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) w[k] = sbN * d[k];
+            for (int k = 0; k < 6; ++k) w[k] = (TT)(sbN * d[k]);
         } else {
             // J2 (Section 4.2) or visco-plasticity (Section 4.3), elastic
             // trial state. The visco-plastic backward-Euler equation
@@ -201,21 +201,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
                 }
                 const double f = 1.5 * inv_seq;
                 const double gdg = g2e * dg;
-                double Nn[6];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    sig[c] = s[c] - gdg * Nn[c];
-                    ep[c] += dg * Nn[c];
-                }
                 const double dgs = dg * inv_seq;
                 g2 = g2e - 6.0 * G * G * dgs;
                 const double b = 4.0 * G * G * (dgs - inv_h3);
-                const double sb = sqrt(fabs(b));
                 if (b > 0.0) kneg = true;
+                if constexpr (sizeof(TT) == 4) {
+                    // FP32 tangent: N = f s is not formed (sigma = (1 - 2G dgamma f) s,
+                    // eps_p += dgamma f s), and w = sqrt(|b|) N, stored in FP32, is
+                    // formed in FP32; the kernel is bound by FP64 arithmetic
+                    const double c1 = 1.0 - gdg * f, c2 = dg * f;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) w[c] = sb * Nn[c];
+                    for (int c = 0; c < 6; ++c) {
+                        sig[c] = c1 * s[c];
+                        ep[c] += c2 * s[c];
+                    }
+                    const float sf = sqrtf(fabsf((float)b)) * (float)f;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) w[c] = sf * (float)s[c];
+                } else {
+                    double Nn[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        sig[c] = s[c] - gdg * Nn[c];
+                        ep[c] += dg * Nn[c];
+                    }
+                    const double sb = sqrt(fabs(b));
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) w[c] = (TT)(sb * Nn[c]);
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) sig[c] = s[c];
@@ -237,11 +252,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
         if (tg) {
             tg[v] = (TT)(kneg ? -K : K);
             tg[cs + v] = (TT)g2;
-            tg[2 * cs + v] = (TT)w[0];
-            tg[3 * cs + v] = (TT)w[1];
-            tg[4 * cs + v] = (TT)w[3];
-            tg[5 * cs + v] = (TT)w[4];
-            tg[6 * cs + v] = (TT)w[5];
+            tg[2 * cs + v] = w[0];
+            tg[3 * cs + v] = w[1];
+            tg[4 * cs + v] = w[3];
+            tg[5 * cs + v] = w[4];
+            tg[6 * cs + v] = w[5];
         }
         acc[0] += frob<double>(sig, sig);
 #pragma unroll
