@@ -381,6 +381,7 @@ static int launch_constitutive(fftg_handle* h, const int* mask_dev, int ncells, 
     a.tie = 1e-12;
     a.dt = h->opt.dt;
     a.elastic_only = elastic_only ? 1 : 0;
+    a.skip_sums = write_history ? 0 : 1;  // Sigma is read after the commit's call only
     a.active = mask_dev ? mask_dev + cell0 : nullptr;
     a.cell_fields = 6 * h->cs;
     a.cell_scalar = h->cs;

@@ -46,6 +46,8 @@ struct ConstArgs {
     CGState* cg;             // if set: cg->floor2 from ||sigma||
     double tie;              // plastic iff Phi_trial > tie * sigma_y
     double dt;               // time step of the increment (visco-plastic phases)
+    int skip_sums;           // 1: nd->sum (the sums of sigma) is left at 0; only the
+                             // commit's call, which writes the history, needs it
     int elastic_only;        // 1: J2 and visco-plastic phases skip the return
                              // (sigma = C_e : (eps - eps_p), the stress of a
                              // committed state); non-linear elastic phases
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
         const double tr = e[0] + e[1] + e[2];
         const double m = tr * (1.0 / 3.0);
         double sig[6];
-        double g2;
+        TT g2t;  // 2G_eff of the tangent, in the tangent's precision
         TT w[6] = {TT(0), TT(0), TT(0), TT(0), TT(0), TT(0)};  // in the tangent's precision
         double dg = 0.0;
         bool kneg = false;  // N(x)N coefficient of the tangent positive
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
             const double eeq = sqrt((2.0 / 3.0) * frob<double>(d, d));
             const double e0r = mp[5];
             const double c = eeq > 0.0 ? sy / eeq * pow(eeq / e0r, nh) : (nh == 1.0 ? sy / e0r : 0.0);
-            g2 = (2.0 / 3.0) * c;
+            const double g2 = (2.0 / 3.0) * c;
+            g2t = (TT)g2;
 #pragma unroll
             for (int k = 0; k < 6; ++k) sig[k] = g2 * d[k];
             const double b = c * (nh - 1.0);
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
             const double eb_h = visco ? 0.0 : eb;
             const bool linear = nh == 1.0;
             const double phi = seq - (sy_h + Hh * (linear ? eb_h : pow(eb_h, nh)));
-            g2 = g2e;
+            g2t = (TT)g2e;
             if (!a.elastic_only && phi > a.tie * sy) {
                 double inv_seq, inv_h3;
                 if (linear) {
@@ -202,23 +205,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
                 const double f = 1.5 * inv_seq;
                 const double gdg = g2e * dg;
                 const double dgs = dg * inv_seq;
-                g2 = g2e - 6.0 * G * G * dgs;
-                const double b = 4.0 * G * G * (dgs - inv_h3);
-                if (b > 0.0) kneg = true;
+                const double bd = dgs - inv_h3;  // b = 4 G^2 bd
+                if (bd > 0.0) kneg = true;
                 if constexpr (sizeof(TT) == 4) {
                     // FP32 tangent: N = f s is not formed (sigma = (1 - 2G dgamma f) s,
-                    // eps_p += dgamma f s), and w = sqrt(|b|) N, stored in FP32, is
-                    // formed in FP32; the kernel is bound by FP64 arithmetic
+                    // eps_p += dgamma f s), and the tangent's coefficients and
+                    // w = sqrt(|b|) N, stored in FP32, are formed in FP32; the
+                    // kernel is bound by FP64 arithmetic
                     const double c1 = 1.0 - gdg * f, c2 = dg * f;
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         sig[c] = c1 * s[c];
                         ep[c] += c2 * s[c];
                     }
-                    const float sf = sqrtf(fabsf((float)b)) * (float)f;
+                    const float Gf = (float)G, dgsf = (float)dgs;
+                    g2t = 2.0f * Gf - 6.0f * Gf * Gf * dgsf;
+                    const float sf = sqrtf(4.0f * Gf * Gf * fabsf((float)bd)) * (float)f;
 #pragma unroll
                     for (int c = 0; c < 6; ++c) w[c] = sf * (float)s[c];
                 } else {
+                    g2t = (TT)(g2e - 6.0 * G * G * dgs);
+                    const double b = 4.0 * G * G * bd;
                     double Nn[6];
 #pragma unroll
                     for (int c = 0; c < 6; ++c) Nn[c] = f * s[c];
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
         if (epbar_new) epbar_new[v] = eb + dg;
         if (tg) {
             tg[v] = (TT)(kneg ? -K : K);
-            tg[cs + v] = (TT)g2;
+            tg[cs + v] = g2t;
             tg[2 * cs + v] = w[0];
             tg[3 * cs + v] = w[1];
             tg[4 * cs + v] = w[3];
@@ -259,8 +266,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_constitutive(ConstArgs a) {
             tg[6 * cs + v] = w[5];
         }
         acc[0] += frob<double>(sig, sig);
+        if (!a.skip_sums) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[1 + c] += sig[c];
+            for (int c = 0; c < 6; ++c) acc[1 + c] += sig[c];
+        }
     }
     double part[7];
 #pragma unroll
