@@ -26,6 +26,8 @@
 
 #include <type_traits>
 
+#include "dd.cuh"
+
 // Twiddles inside the FP32 register DFTs: 1 = compile-time constants
 // (immediate operands), 0 = read from the shared-memory table. FP64 DFTs
 // always read the table (measured faster at 243^3: 3.14 against 3.19 ms for
@@ -71,6 +73,21 @@ __device__ __forceinline__ cplx<T> twmul(cplx<T> v, cplx<T> w) {
     return S < 0 ? cmul(v, w) : cmulc(v, w);
 }
 
+// x / 2, and -x where S < 0: exact operations. For double-float pairs both
+// words are scaled or negated, which gives the same bits as the general
+// double-float product by 0.5 or by +-1 at a fraction of its cost.
+template <typename T>
+__device__ __forceinline__ cplx<T> half_of(cplx<T> a) { return T(0.5) * a; }
+template <>
+__device__ __forceinline__ cplx<dd> half_of<dd>(cplx<dd> a) {
+    return mk(dd(0.5f * a.x.hi, 0.5f * a.x.lo), dd(0.5f * a.y.hi, 0.5f * a.y.lo));
+}
+template <int S, typename T>
+__device__ __forceinline__ cplx<T> signed_by(cplx<T> a) {
+    if constexpr (S < 0) return mk(-a.x, -a.y);
+    else return a;
+}
+
 // ---------------------------------------------------------------- butterflies
 // DFT of 3 or 5 points with kernel exp(S * 2 pi i jk / P), in place.
 template <int P, int S, typename T>
@@ -82,9 +99,9 @@ struct Butterfly<3, S, T> {
         const T h = T(0.86602540378443864676);  // sqrt(3)/2
         cplx<T> t1 = a[1] + a[2];
         cplx<T> t2 = a[1] - a[2];
-        cplx<T> m = a[0] - T(0.5) * t1;
+        cplx<T> m = a[0] - half_of(t1);
         cplx<T> r = mul_i(t2);
-        r = T(S) * h * r;
+        r = h * signed_by<S>(r);
         a[0] = a[0] + t1;
         a[1] = m + r;
         a[2] = m - r;
@@ -104,8 +121,8 @@ struct Butterfly<5, S, T> {
         cplx<T> A2 = a[0] + c2 * b1 + c1 * b2;
         cplx<T> B1 = mul_i(s1 * d1 + s2 * d2);
         cplx<T> B2 = mul_i(s2 * d1 - s1 * d2);
-        B1 = T(S) * B1;
-        B2 = T(S) * B2;
+        B1 = signed_by<S>(B1);
+        B2 = signed_by<S>(B2);
         a[0] = a[0] + b1 + b2;
         a[1] = A1 + B1;
         a[4] = A1 - B1;

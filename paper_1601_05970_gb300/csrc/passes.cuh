@@ -527,7 +527,7 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
     const cplx<T> t0 = n0 * c[0] + n1 * c[5] + n2 * c[4];
     const cplx<T> t1 = n0 * c[5] + n1 * c[1] + n2 * c[3];
     const cplx<T> t2 = n0 * c[4] + n1 * c[3] + n2 * c[2];
-    const cplx<T> h = T(-0.5) * (n0 * t0 + n1 * t1 + n2 * t2);
+    const cplx<T> h = signed_by<-1>(half_of(n0 * t0 + n1 * t1 + n2 * t2));  // -(n.t)/2, exactly
     const cplx<T> u0 = t0 + n0 * h, u1 = t1 + n1 * h, u2 = t2 + n2 * h;
     const T m0 = scale * n0, m1 = scale * n1, m2 = scale * n2;
     b[0 * cs] = (T(2) * m0) * u0;
