@@ -115,7 +115,9 @@ __host__ __device__ __forceinline__ bool operator>(dd a, dd b) {
 }
 __host__ __device__ __forceinline__ bool operator<(dd a, dd b) { return b > a; }
 
+#ifdef __CUDACC__
 // 1/sqrt(x) for the per-frequency factors of Ghat (FP64 rsqrt, rounded)
 __device__ __forceinline__ dd rsqrt_t(dd x) { return dd(rsqrt((double)x)); }
+#endif
 
 }  // namespace fftg
