@@ -325,10 +325,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_FS_P1_MINB : 1
         for (int c = 0; c < kFsPairs; ++c) {
             const cplx<T> zk = z[(c * R + row) * N + pk];
             const cplx<T> zn = conj(z[(c * R + row) * N + pn]);
-            out[(2 * c) * HS + o] = T(0.5) * (zk + zn);
+            out[(2 * c) * HS + o] = half_of(zk + zn);
             if (2 * c + 1 < kFsComp) {
                 const cplx<T> d = zk - zn;
-                out[(2 * c + 1) * HS + o] = mk(T(0.5) * d.y, T(-0.5) * d.x);
+                out[(2 * c + 1) * HS + o] = half_of(mk(d.y, -d.x));
             }
         }
     }

@@ -435,9 +435,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? FFTG_P1_MINB : is_d
         for (int c = 0; c < 3; ++c) {
             const cplx<T> zk = z[(c * R + row) * N + pk];
             const cplx<T> zn = conj(z[(c * R + row) * N + pn]);
-            const cplx<T> A = T(0.5) * (zk + zn);
+            const cplx<T> A = half_of(zk + zn);
             const cplx<T> d = zk - zn;  // (zk - zn) / (2i) = (d.y, -d.x) / 2
-            const cplx<T> B = mk(T(0.5) * d.y, T(-0.5) * d.x);
+            const cplx<T> B = half_of(mk(d.y, -d.x));
             out[(2 * c) * HS + o] = A;
             out[(2 * c + 1) * HS + o] = B;
         }
@@ -530,9 +530,9 @@ __device__ __forceinline__ void ghat_point(cplx<T>* b, int cs, int f1, int f2, i
     const cplx<T> h = signed_by<-1>(half_of(n0 * t0 + n1 * t1 + n2 * t2));  // -(n.t)/2, exactly
     const cplx<T> u0 = t0 + n0 * h, u1 = t1 + n1 * h, u2 = t2 + n2 * h;
     const T m0 = scale * n0, m1 = scale * n1, m2 = scale * n2;
-    b[0 * cs] = (T(2) * m0) * u0;
-    b[1 * cs] = (T(2) * m1) * u1;
-    b[2 * cs] = (T(2) * m2) * u2;
+    b[0 * cs] = (m0 + m0) * u0;  // 2 m, exactly
+    b[1 * cs] = (m1 + m1) * u1;
+    b[2 * cs] = (m2 + m2) * u2;
     b[3 * cs] = m1 * u2 + m2 * u1;
     b[4 * cs] = m0 * u2 + m2 * u0;
     b[5 * cs] = m0 * u1 + m1 * u0;
