@@ -188,3 +188,26 @@ def test_projection_self_adjoint_and_idempotent():
     assert np.abs(O.project(Gx) - Gx).max() < 1e-12 * np.abs(Gx).max()
     # G x + (I - G) x splits into compatible and equilibrated parts
     assert abs(O.inner(Gx, x - Gx)) < 1e-10 * O.inner(x, x)
+
+
+def test_ghat_through_t_equals_appendix_a():
+    # The fused P3 applies Ghat through t = tau n alone, as n(x)u + u(x)n
+    # with u = t - (n.t / 2) n: the same operator as Appendix A's
+    # Ghat_ijlm tau_lm (the oracle's explicit 3x3x3x3 array), for complex
+    # symmetric tau and any xi != 0. Dropping the 1/2 breaks it.
+    rng = _rng(21)
+    for _ in range(50):
+        xi = rng.integers(-121, 122, size=3).astype(np.float64)
+        if not xi.any():
+            continue
+        a = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        tau = a + a.T
+        ref = np.einsum("ijlm,lm->ij", O.ghat(xi), tau)
+        n = xi / np.linalg.norm(xi)
+        t = tau @ n
+        u = t - 0.5 * (n @ t) * n
+        got = np.outer(n, u) + np.outer(u, n)
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(tau).max()
+        wrong = t - (n @ t) * n
+        bad = np.outer(n, wrong) + np.outer(wrong, n)
+        assert np.abs(bad - ref).max() > 1e-3 * np.abs(ref).max() or np.abs(n @ t) < 1e-12

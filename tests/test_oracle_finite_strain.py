@@ -295,3 +295,20 @@ def test_macro_tangent_of_the_laminate_matches_the_closed_form():
         Cfd[:, col] = ((_laminate_closed_form(np.eye(3) + dF + E, f, I.SVK_HARD, I.SVK_SOFT)
                         - _laminate_closed_form(np.eye(3) + dF - E, f, I.SVK_HARD, I.SVK_SOFT)) / (2 * h)).reshape(9)
     assert np.abs(C - Cfd).max() <= 1e-6 * np.abs(C).max()
+
+
+def test_ghat_fs_row_form():
+    # The fused finite-strain P3 takes row i of Ghat_fs : A as (A_i . n) n,
+    # n = xi / |xi|: the oracle's delta_il xi_j xi_m / |xi|^2 contracted
+    # with A_lm, for complex A and any xi != 0.
+    rng = np.random.default_rng(22)
+    for _ in range(50):
+        xi = rng.integers(-121, 122, size=3).astype(np.float64)
+        if not xi.any():
+            continue
+        A = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        ref = np.einsum("ijlm,lm->ij", FS.ghat_fs(xi), A)
+        n = xi / np.linalg.norm(xi)
+        got = np.outer(A @ n, n)
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(A).max()
+        assert np.abs(np.outer(n, A @ n) - ref).max() > 1e-6 * np.abs(ref).max()  # the transpose is not it
