@@ -76,3 +76,45 @@ def test_double_float_arithmetic(tmp_path):
     assert worst_mul <= 2.0 ** -44                                    # product with cross terms
     # and not merely FP32 (2^-24)
     assert max(worst_add, worst_mul) > 0.0
+
+
+EXACT = r"""
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include "dd.cuh"
+using fftg::dd;
+static bool same(dd a, dd b) { return std::memcmp(&a, &b, sizeof(dd)) == 0; }
+int main() {
+    std::mt19937_64 g(4242);
+    std::uniform_real_distribution<double> m(-1.0, 1.0);
+    std::uniform_int_distribution<int> ex(-30, 30);
+    long long bad_half = 0, bad_neg = 0, bad_twice = 0;
+    const dd half(0.5), minus1(-1), two(2);
+    for (int i = 0; i < 200000; ++i) {
+        const dd x(std::ldexp(m(g), ex(g)));
+        if (!same(half * x, dd(0.5f * x.hi, 0.5f * x.lo))) ++bad_half;
+        if (!same(minus1 * x, -x)) ++bad_neg;
+        if (!same(two * x, x + x)) ++bad_twice;
+    }
+    std::printf("%lld %lld %lld\n", bad_half, bad_neg, bad_twice);
+    return 0;
+}
+"""
+
+
+def test_exact_scalings_match_the_general_products(tmp_path):
+    """The butterflies, the real-to-complex split and Ghat halve, negate and
+    double double-float pairs word by word instead of multiplying by 0.5,
+    -1 and 2: on normalised pairs the general product gives the same bits."""
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    src = tmp_path / "exact_host.cu"
+    src.write_text(EXACT)
+    exe = tmp_path / "exact_host"
+    subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-ffp-contract=off",
+                    "-I", CSRC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert list(map(int, out)) == [0, 0, 0]
